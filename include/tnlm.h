@@ -1,0 +1,175 @@
+/*
+ * tnlm.h -- C ABI of the GB300 (sm_103a) TNLM 4DCT reconstruction library.
+ *
+ * Method: Tian, Jia, Dong, Lou, Jiang, "Low-dose 4DCT reconstruction via
+ * temporal non-local means", arXiv:1009.1351.  All N respiratory phases of
+ * one slice are reconstructed together by minimising Eq. 1 with the
+ * modified forward-backward splitting of Sec. 2.2:
+ *
+ *   repeat K times (TNLM algorithm box):
+ *     g_i   = CGLS data step from f_i^(k-1)           (CGLS box; or Eq. 4)
+ *     omega = Eq. 8 weights between adjacent phases from g   (Sec. 2.3 window)
+ *     f     = M2 Gauss-Jacobi sweeps of Eq. 7 from g   (Gauss-Jacobi box)
+ *     f     = max(f, 0)                                (positivity step)
+ *
+ * Conventions shared by every call
+ *   - Phases are 0..N-1 (the paper's 1..N) and cyclic: f_N = f_0 (Sec. 2.1).
+ *   - Images are float32 [N][ny][nx], row-major, ix fastest.  Pixel (ix, iy)
+ *     has centre ((ix-(nx-1)/2)*pixel_mm, (iy-(ny-1)/2)*pixel_mm) and covers
+ *     the half-open square of side pixel_mm around it.  Values are linear
+ *     attenuation in 1/mm.
+ *   - Sinograms are float32 [N][V][B]: phase, view, detector bin.  View v of
+ *     phase i has source angle view_angles_rad[i*V + v]; the source sits at
+ *     sid_mm*(cos t, sin t).  The detector is an equiangular arc centred on
+ *     the source (the arc detector of Sec. 3); bin b has fan angle
+ *     (b-(B-1)/2)*bin_mm/sdd_mm, counter-clockwise from the central ray.
+ *   - P_i is the exact-length ray-driven projector: entry (ray, pixel) is the
+ *     length in mm of the ray inside the pixel square (the quantity Siddon's
+ *     method traces, Sec. 3).
+ *   - Device pointers are CUDA global-memory pointers on the geometry's
+ *     device, 16-byte aligned, owned by the caller; the library never frees
+ *     them.  'stream' is a cudaStream_t (NULL = legacy default stream).  All
+ *     calls are asynchronous on that stream unless stated otherwise.
+ *   - Every call returns a tnlm_status; on failure tnlm_last_error() (per
+ *     host thread) describes it.  Argument checks happen before any GPU work.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef TNLM_H
+#define TNLM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TNLM_OK = 0,
+    TNLM_ERR_INVALID_ARG = 1, /* a size, pointer, parameter or geometry check failed */
+    TNLM_ERR_OOM = 2,         /* device workspace allocation failed (nothing leaked) */
+    TNLM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
+    TNLM_ERR_NUMERIC = 4,     /* a non-finite value was met in the weights or images */
+    TNLM_ERR_TIMEOUT = 5      /* reserved for bounded device waits */
+} tnlm_status;
+
+enum { TNLM_DETECTOR_ARC = 0 };
+enum { TNLM_DATA_CGLS = 0, TNLM_DATA_GRAD = 1 };
+
+/* Scan geometry of one slice (Sec. 2.1: P_i maps f_i to the views of phase i). */
+typedef struct {
+    int nx, ny;                    /* image size in pixels, 1..8192 */
+    double pixel_mm;               /* pixel side, > 0 */
+    int n_phases;                  /* N in 3..4096 (with N = 2 both neighbours coincide) */
+    int n_views;                   /* V >= 1 views per phase */
+    int n_bins;                    /* B detector bins, 1..4096 */
+    double bin_mm;                 /* bin pitch on the arc, > 0 */
+    double sid_mm;                 /* source to isocentre; > image half-diagonal */
+    double sdd_mm;                 /* source to detector; > sid_mm + image half-diagonal */
+    int detector;                  /* TNLM_DETECTOR_ARC */
+    const double* view_angles_rad; /* host [N*V] source angles, copied at creation */
+    int device;                    /* CUDA device ordinal */
+} tnlm_geometry_desc;
+
+typedef struct tnlm_geometry tnlm_geometry;
+
+/* Iteration parameters (Sec. 2.2; the paper leaves their values open). */
+typedef struct {
+    double mu_hat;   /* mu/beta of Eq. 7, >= 0 */
+    double h;        /* kernel width of Eq. 8 (image units), > 0 */
+    double beta;     /* step constant of Eq. 4 (data_step = GRAD only), > 0 */
+    int patch;       /* d: odd patch side, 1..15 */
+    int window;      /* W: odd search-window side, 1..31 */
+    int m1;          /* CGLS steps per outer iteration, >= 0 (0: g = f^(k-1)) */
+    int m2;          /* Gauss-Jacobi sweeps per outer iteration, >= 0 */
+    int k_outer;     /* outer iterations K, >= 0 */
+    int data_step;   /* TNLM_DATA_CGLS (CGLS box) or TNLM_DATA_GRAD (Eq. 4) */
+    int clamp;       /* 1: f = max(f, 0) after each outer iteration */
+    double tol;      /* > 0: stop once ||f^k - f^(k-1)|| / ||f^k|| < tol (checked on
+                        the host every 'tol_check_every' iterations); 0: run K */
+    int tol_check_every; /* >= 1 when tol > 0 */
+} tnlm_params;
+
+/* Host-side report of tnlm_reconstruct (all FP64 values come from FP64
+ * device reductions). */
+typedef struct {
+    int iterations;          /* outer iterations executed */
+    double rel_change;       /* ||f^k - f^(k-1)||_2 / ||f^k||_2 of the last one */
+    double data_residual;    /* sum_i ||Sigma^{-1/2}(P_i f_i - y_i)||^2 at the start of
+                                the last outer iteration (i.e. of f^(k-1)) */
+    double* rel_change_hist; /* optional caller-owned host array [k_outer] or NULL */
+    double* residual_hist;   /* optional caller-owned host array [k_outer] or NULL */
+} tnlm_report;
+
+/* Create a geometry handle on desc->device.  The library copies the view
+ * angles and builds its per-view / per-bin / per-ray tables on the device.
+ * Errors: TNLM_ERR_INVALID_ARG (see the field comments above), TNLM_ERR_OOM,
+ * TNLM_ERR_CUDA.  *out is NULL on failure. */
+tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* desc, tnlm_geometry** out);
+
+/* Free the handle, its tables and its cached workspace.  NULL is a no-op.
+ * Synchronises the handle's device. */
+void tnlm_destroy_geometry(tnlm_geometry* geom);
+
+/* d_sino[i] = P_i d_img[i] for every phase (Eq. 1).  In: image [N][ny][nx];
+ * out: sinogram [N][V][B], overwritten. */
+tnlm_status tnlm_project(const tnlm_geometry* geom, const float* d_img, float* d_sino,
+                         void* stream);
+
+/* d_img[i] = P_i^T d_sino[i] (the adjoint used by the CGLS box and Eq. 4):
+ * the exact transpose of tnlm_project, computed as an atomic-free gather.
+ * In: sinogram [N][V][B]; out: image [N][ny][nx], overwritten. */
+tnlm_status tnlm_backproject(const tnlm_geometry* geom, const float* d_sino, float* d_img,
+                             void* stream);
+
+/* Byte sizes of the two output buffers of tnlm_weights. */
+tnlm_status tnlm_weights_size(const tnlm_geometry* geom, const tnlm_params* params,
+                              size_t* dist_bytes, size_t* norm_bytes);
+
+/* Eq. 8 weights between every pair of adjacent phases, computed from the
+ * images d_g (the CGLS output g^(k) in the algorithm).  One distance array
+ * serves both directions of a pair (the symmetric reuse of Sec. 2.3):
+ *
+ *   d_dist [N][W*W][ny][nx]: D_i(x, s) = ||R_{g_i}(x) - R_{g_{i+1}}(x+s)||^2,
+ *       the squared L2 distance of the d x d patches (values outside the
+ *       image count as 0), for shift s = (sx, sy), index (sy+r)*W + (sx+r),
+ *       r = (W-1)/2; +INFINITY where x+s lies outside the image.
+ *   d_norm [4][N][ny][nx]: per row phase i and pixel x, the stabiliser m and
+ *       the normaliser Z of each direction:
+ *         [0] m_next, [1] Z_next:  omega_{i,i+1}(x, x+s) = exp(-(D_i(x,s) - m_next)/h^2) / Z_next
+ *         [2] m_prev, [3] Z_prev:  omega_{i,i-1}(x, x+s) = exp(-(D_{i-1}(x+s,-s) - m_prev)/h^2) / Z_prev
+ *       m is the row minimum of D, so Z >= 1, and each row sums to 1 (Eq. 3).
+ * Uses the handle's cached workspace (allocated on first use). */
+tnlm_status tnlm_weights(const tnlm_geometry* geom, const tnlm_params* params, const float* d_g,
+                         float* d_dist, float* d_norm, void* stream);
+
+/* Workspace the handle allocates for tnlm_reconstruct / tnlm_weights with
+ * these parameters (it is cached and reused between calls). */
+tnlm_status tnlm_workspace_bytes(const tnlm_geometry* geom, const tnlm_params* params,
+                                 size_t* bytes);
+
+/* The TNLM algorithm box: K outer iterations from d_f = f^(0) (for the
+ * paper, the FBP of all views), result f^(K) written back into d_f.
+ *   d_y    [N][V][B]  measured line integrals y_i
+ *   d_winv [N][V][B]  Sigma^{-1} (diagonal inverse variance, Eq. 9), >= 0
+ *   d_f    [N][ny][nx] in: f^(0), out: f^(K)
+ *   rep    host report or NULL.  With rep != NULL (or tol > 0) the call
+ *          synchronises the stream and checks the device numeric flag;
+ *          without, it returns as soon as the work is queued and a numeric
+ *          fault is reported by the next synchronising call.
+ * Errors: TNLM_ERR_INVALID_ARG, TNLM_ERR_OOM, TNLM_ERR_CUDA, TNLM_ERR_NUMERIC. */
+tnlm_status tnlm_reconstruct(const tnlm_geometry* geom, const tnlm_params* params,
+                             const float* d_y, const float* d_winv, float* d_f,
+                             tnlm_report* rep, void* stream);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char* tnlm_last_error(void);
+
+/* Test hook for failure handling: the n-th device allocation from now on
+ * (n >= 1) fails as if the device were out of memory; n = 0 disables. */
+void tnlm_debug_fail_alloc_after(int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TNLM_H */

@@ -1,0 +1,229 @@
+"""GB300-native TNLM 4DCT reconstruction (arXiv:1009.1351).
+
+Thin Python binding of the C ABI declared in include/tnlm.h.  Every function
+here only marshals arguments (torch CUDA tensors or raw device pointers,
+the CUDA stream) and calls the library of the same name; all computation
+runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library has not been built (``python -c "import __graft_entry__ as g;
+g.build()"``) or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Any, Dict, Optional, Tuple
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libtnlm.so")
+
+TNLM_OK = 0
+TNLM_ERR_INVALID_ARG = 1
+TNLM_ERR_OOM = 2
+TNLM_ERR_CUDA = 3
+TNLM_ERR_NUMERIC = 4
+TNLM_ERR_TIMEOUT = 5
+TNLM_DETECTOR_ARC = 0
+TNLM_DATA_CGLS = 0
+TNLM_DATA_GRAD = 1
+
+EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tnlm_backproject",
+            "tnlm_weights_size", "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct",
+            "tnlm_last_error", "tnlm_debug_fail_alloc_after")
+
+
+class GeometryDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("pixel_mm", ctypes.c_double),
+                ("n_phases", ctypes.c_int), ("n_views", ctypes.c_int), ("n_bins", ctypes.c_int),
+                ("bin_mm", ctypes.c_double), ("sid_mm", ctypes.c_double),
+                ("sdd_mm", ctypes.c_double), ("detector", ctypes.c_int),
+                ("view_angles_rad", ctypes.POINTER(ctypes.c_double)), ("device", ctypes.c_int)]
+
+
+class ParamsC(ctypes.Structure):
+    _fields_ = [("mu_hat", ctypes.c_double), ("h", ctypes.c_double), ("beta", ctypes.c_double),
+                ("patch", ctypes.c_int), ("window", ctypes.c_int), ("m1", ctypes.c_int),
+                ("m2", ctypes.c_int), ("k_outer", ctypes.c_int), ("data_step", ctypes.c_int),
+                ("clamp", ctypes.c_int), ("tol", ctypes.c_double),
+                ("tol_check_every", ctypes.c_int)]
+
+
+class ReportC(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("rel_change", ctypes.c_double),
+                ("data_residual", ctypes.c_double),
+                ("rel_change_hist", ctypes.POINTER(ctypes.c_double)),
+                ("residual_hist", ctypes.POINTER(ctypes.c_double))]
+
+
+class TnlmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tnlm status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libtnlm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.tnlm_create_geometry.argtypes = [ctypes.POINTER(GeometryDesc), ctypes.POINTER(vp)]
+    lib.tnlm_destroy_geometry.argtypes = [vp]
+    lib.tnlm_destroy_geometry.restype = None
+    lib.tnlm_project.argtypes = [vp, vp, vp, vp]
+    lib.tnlm_backproject.argtypes = [vp, vp, vp, vp]
+    lib.tnlm_weights_size.argtypes = [vp, ctypes.POINTER(ParamsC), ctypes.POINTER(ctypes.c_size_t),
+                                      ctypes.POINTER(ctypes.c_size_t)]
+    lib.tnlm_weights.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp, vp]
+    lib.tnlm_workspace_bytes.argtypes = [vp, ctypes.POINTER(ParamsC), ctypes.POINTER(ctypes.c_size_t)]
+    lib.tnlm_reconstruct.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp,
+                                     ctypes.POINTER(ReportC), vp]
+    lib.tnlm_last_error.restype = ctypes.c_char_p
+    lib.tnlm_debug_fail_alloc_after.argtypes = [ctypes.c_int]
+    lib.tnlm_debug_fail_alloc_after.restype = None
+    for name in ("tnlm_create_geometry", "tnlm_project", "tnlm_backproject", "tnlm_weights_size",
+                 "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != TNLM_OK:
+        msg = load_library().tnlm_last_error().decode(errors="replace")
+        raise TnlmError(status, msg)
+
+
+def _ptr(t: Any) -> Optional[int]:
+    """Device pointer of a torch CUDA tensor (float32, contiguous) or a raw int."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    import torch
+    if t.dtype != torch.float32:
+        raise ValueError("expected float32")
+    return t.data_ptr()
+
+
+def _stream(stream: Any) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def params_c(p: Any) -> ParamsC:
+    """Marshal an object with the tnlm_params fields (e.g. synth.Params)."""
+    return ParamsC(float(p.mu_hat), float(p.h), float(getattr(p, "beta", 0.0)), int(p.patch),
+                   int(p.window), int(p.m1), int(p.m2), int(p.k_outer),
+                   int(getattr(p, "data_step", 0)), int(getattr(p, "clamp", 1)),
+                   float(getattr(p, "tol", 0.0)), int(getattr(p, "tol_check_every", 1)))
+
+
+class Geometry:
+    """Owns a tnlm_geometry handle (created by tnlm_create_geometry)."""
+
+    def __init__(self, handle: int, desc: GeometryDesc):
+        self.handle = handle
+        self.nx, self.ny = desc.nx, desc.ny
+        self.n_phases, self.n_views, self.n_bins = desc.n_phases, desc.n_views, desc.n_bins
+
+    @property
+    def img_shape(self) -> Tuple[int, int, int]:
+        return (self.n_phases, self.ny, self.nx)
+
+    @property
+    def sino_shape(self) -> Tuple[int, int, int]:
+        return (self.n_phases, self.n_views, self.n_bins)
+
+    def close(self) -> None:
+        if self.handle:
+            load_library().tnlm_destroy_geometry(ctypes.c_void_p(self.handle))
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def tnlm_create_geometry(g: Any, angles=None, device: int = 0) -> Geometry:
+    """g: an object with nx, ny, pixel_mm, n_phases, n_views, n_bins, bin_mm,
+    sid_mm, sdd_mm (e.g. synth.Geometry); angles: [N*V] source angles."""
+    import numpy as np
+    ang = np.ascontiguousarray(g.view_angles() if angles is None else angles, dtype=np.float64)
+    desc = GeometryDesc(int(g.nx), int(g.ny), float(g.pixel_mm), int(g.n_phases), int(g.n_views),
+                        int(g.n_bins), float(g.bin_mm), float(g.sid_mm), float(g.sdd_mm),
+                        TNLM_DETECTOR_ARC, ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        int(device))
+    h = ctypes.c_void_p()
+    _check(load_library().tnlm_create_geometry(ctypes.byref(desc), ctypes.byref(h)))
+    return Geometry(h.value, desc)
+
+
+def tnlm_project(geom: Geometry, img, sino, stream=None) -> None:
+    _check(load_library().tnlm_project(geom.handle, _ptr(img), _ptr(sino), _stream(stream)))
+
+
+def tnlm_backproject(geom: Geometry, sino, img, stream=None) -> None:
+    _check(load_library().tnlm_backproject(geom.handle, _ptr(sino), _ptr(img), _stream(stream)))
+
+
+def tnlm_weights_size(geom: Geometry, params) -> Tuple[int, int]:
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    pc = params_c(params)
+    _check(load_library().tnlm_weights_size(geom.handle, ctypes.byref(pc), ctypes.byref(a),
+                                            ctypes.byref(b)))
+    return a.value, b.value
+
+
+def tnlm_workspace_bytes(geom: Geometry, params) -> int:
+    a = ctypes.c_size_t()
+    pc = params_c(params)
+    _check(load_library().tnlm_workspace_bytes(geom.handle, ctypes.byref(pc), ctypes.byref(a)))
+    return a.value
+
+
+def tnlm_weights(geom: Geometry, params, g, dist, norm, stream=None) -> None:
+    pc = params_c(params)
+    _check(load_library().tnlm_weights(geom.handle, ctypes.byref(pc), _ptr(g), _ptr(dist),
+                                       _ptr(norm), _stream(stream)))
+
+
+def tnlm_reconstruct(geom: Geometry, params, y, winv, f, report: bool = True,
+                     stream=None) -> Optional[Dict[str, Any]]:
+    """Run the TNLM iteration in place on f.  With report=True the call
+    synchronises and returns the report (iterations, final relative change,
+    data residual and their per-iteration histories)."""
+    pc = params_c(params)
+    lib = load_library()
+    if not report:
+        _check(lib.tnlm_reconstruct(geom.handle, ctypes.byref(pc), _ptr(y), _ptr(winv), _ptr(f),
+                                    None, _stream(stream)))
+        return None
+    k = max(int(pc.k_outer), 1)
+    rel = (ctypes.c_double * k)()
+    res = (ctypes.c_double * k)()
+    rep = ReportC(0, 0.0, 0.0, rel, res)
+    _check(lib.tnlm_reconstruct(geom.handle, ctypes.byref(pc), _ptr(y), _ptr(winv), _ptr(f),
+                                ctypes.byref(rep), _stream(stream)))
+    n = rep.iterations
+    return {"iterations": n, "rel_change": rep.rel_change, "data_residual": rep.data_residual,
+            "rel_change_hist": list(rel[:n]), "residual_hist": list(res[:n])}
+
+
+def tnlm_debug_fail_alloc_after(n: int) -> None:
+    load_library().tnlm_debug_fail_alloc_after(int(n))

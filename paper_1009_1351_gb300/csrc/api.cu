@@ -1,0 +1,488 @@
+// C ABI of the TNLM library: argument checks, geometry tables, workspace and
+// the outer iteration of the TNLM algorithm box (Sec. 2.2).
+#include "internal.cuh"
+
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <vector>
+
+using namespace tnlm;
+
+namespace {
+
+thread_local char g_err[512] = "";
+std::atomic<int> g_fail_after{0};
+
+tnlm_status fail(tnlm_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+tnlm_status cuda_fail(cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation)
+        return fail(TNLM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(TNLM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+cudaError_t dev_alloc(void** p, size_t n) {
+    *p = nullptr;
+    int f = g_fail_after.load();
+    while (f > 0) {
+        if (g_fail_after.compare_exchange_weak(f, f - 1)) {
+            if (f == 1) return cudaErrorMemoryAllocation;
+            break;
+        }
+    }
+    return cudaMalloc(p, n);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t err;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        err = cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+tnlm_status check_params(const tnlm_params* p) {
+    if (!p) return fail(TNLM_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->mu_hat >= 0.0) || !isfinite(p->mu_hat))
+        return fail(TNLM_ERR_INVALID_ARG, "mu_hat must be finite and >= 0");
+    if (!(p->h > 0.0) || !isfinite(p->h)) return fail(TNLM_ERR_INVALID_ARG, "h must be finite and > 0");
+    if (p->patch < 1 || p->patch > kMaxPatch || (p->patch & 1) == 0)
+        return fail(TNLM_ERR_INVALID_ARG, "patch must be odd and in [1, %d]", kMaxPatch);
+    if (p->window < 1 || p->window > kMaxWindow || (p->window & 1) == 0)
+        return fail(TNLM_ERR_INVALID_ARG, "window must be odd and in [1, %d]", kMaxWindow);
+    if (p->m1 < 0 || p->m2 < 0 || p->k_outer < 0)
+        return fail(TNLM_ERR_INVALID_ARG, "m1, m2 and k_outer must be >= 0");
+    if (p->m1 > 1000 || p->m2 > 100000 || p->k_outer > 1000000)
+        return fail(TNLM_ERR_INVALID_ARG, "iteration counts out of range");
+    if (p->data_step != TNLM_DATA_CGLS && p->data_step != TNLM_DATA_GRAD)
+        return fail(TNLM_ERR_INVALID_ARG, "data_step must be TNLM_DATA_CGLS or TNLM_DATA_GRAD");
+    if (p->data_step == TNLM_DATA_GRAD && (!(p->beta > 0.0) || !isfinite(p->beta)))
+        return fail(TNLM_ERR_INVALID_ARG, "beta must be finite and > 0 for the gradient step");
+    if (p->clamp != 0 && p->clamp != 1) return fail(TNLM_ERR_INVALID_ARG, "clamp must be 0 or 1");
+    if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(TNLM_ERR_INVALID_ARG, "tol must be >= 0");
+    if (p->tol > 0.0 && p->tol_check_every < 1)
+        return fail(TNLM_ERR_INVALID_ARG, "tol_check_every must be >= 1 when tol > 0");
+    return TNLM_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Byte layout of the workspace for window radius rho and history capacity kcap.
+struct WsLayout {
+    size_t off_u, off_s, off_gr, off_R, off_T, off_r, off_z, off_t, off_sw, off_D, off_U0, off_U1,
+        off_mins, off_zn, off_part, off_part2, off_state, total;
+    size_t part_len, part2_len;
+    PadPlane pp;
+};
+
+WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
+    WsLayout L{};
+    const size_t npx = (size_t)g->nx * g->ny, N = g->N;
+    const size_t nsg = (size_t)g->V * g->B;
+    const int ox = (int)align_up((size_t)rho, 4);
+    L.pp.ox = ox;
+    L.pp.oy = rho;
+    L.pp.px = (int)align_up((size_t)g->nx + 2 * ox, 4);
+    L.pp.py = g->ny + 2 * rho;
+    L.pp.plane = (size_t)L.pp.px * L.pp.py;
+    const size_t W2 = (size_t)(2 * rho + 1) * (2 * rho + 1);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
+    L.off_u = take(4 * npx * N);
+    L.off_s = take(4 * npx * N);
+    L.off_gr = take(4 * npx * N);
+    L.off_R = take(4 * (size_t)g->ny * (g->nx + 4) * N);
+    L.off_T = take(4 * (size_t)g->nx * (g->ny + 4) * N);
+    L.off_r = take(4 * nsg * N);
+    L.off_z = take(4 * nsg * N);
+    L.off_t = take(4 * nsg * N);
+    L.off_sw = take(4 * nsg * N);
+    L.off_D = take(4 * L.pp.plane * W2 * N);
+    L.off_U0 = take(4 * L.pp.plane * N);
+    L.off_U1 = take(4 * L.pp.plane * N);
+    L.off_mins = take(4 * 2 * npx * N);
+    L.off_zn = take(4 * 2 * npx * N);
+    L.part_len = N * (size_t)g->V * proj_chunks(g) + N * (size_t)bp_blocks_per_phase(g);
+    L.part2_len = 2 * (size_t)gj_blocks(g);
+    L.off_part = take(8 * L.part_len);
+    L.off_part2 = take(8 * L.part2_len);
+    // state: gamma, a, b, res0 [N] doubles; hist 2 x kcap doubles; active [N], iter, err ints
+    L.off_state = take(8 * (4 * N + 2 * (size_t)kcap) + 4 * (N + 2));
+    L.total = o;
+    return L;
+}
+
+tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
+    Workspace& ws = g->ws;
+    if (ws.base && ws.rho >= rho && ws.kcap >= kcap) return TNLM_OK;
+    const int nrho = ws.base ? (ws.rho > rho ? ws.rho : rho) : rho;
+    const int nk = ws.base ? (ws.kcap > kcap ? ws.kcap : kcap) : kcap;
+    WsLayout L = ws_layout(g, nrho, nk < 1 ? 1 : nk);
+    void* base = nullptr;
+    cudaError_t e = dev_alloc(&base, L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(TNLM_ERR_OOM, "workspace allocation of %zu bytes failed: %s", L.total,
+                    cudaGetErrorString(e));
+    }
+    if (ws.base) {
+        cudaStreamSynchronize(st);
+        cudaFree(ws.base);
+    }
+    char* b = (char*)base;
+    ws = Workspace{};
+    ws.base = base;
+    ws.bytes = L.total;
+    ws.rho = nrho;
+    ws.kcap = nk < 1 ? 1 : nk;
+    ws.u = (float*)(b + L.off_u);
+    ws.s = (float*)(b + L.off_s);
+    ws.gr = (float*)(b + L.off_gr);
+    ws.R = (float*)(b + L.off_R);
+    ws.T = (float*)(b + L.off_T);
+    ws.r = (float*)(b + L.off_r);
+    ws.z = (float*)(b + L.off_z);
+    ws.t = (float*)(b + L.off_t);
+    ws.sw = (float*)(b + L.off_sw);
+    ws.pp = L.pp;
+    ws.D = (float*)(b + L.off_D);
+    ws.U0 = (float*)(b + L.off_U0);
+    ws.U1 = (float*)(b + L.off_U1);
+    ws.mins = (float*)(b + L.off_mins);
+    ws.zn = (float*)(b + L.off_zn);
+    ws.part = (double*)(b + L.off_part);
+    ws.part_len = L.part_len;
+    ws.part2 = (double*)(b + L.off_part2);
+    const size_t N = g->N;
+    double* sd = (double*)(b + L.off_state);
+    ws.st.gamma = sd;
+    ws.st.a = sd + N;
+    ws.st.b = sd + 2 * N;
+    ws.st.res0 = sd + 3 * N;
+    ws.st.hist_rel = sd + 4 * N;
+    ws.st.hist_res = sd + 4 * N + ws.kcap;
+    int* si = (int*)(sd + 4 * N + 2 * (size_t)ws.kcap);
+    ws.st.active = si;
+    ws.st.iter = si + N;
+    ws.st.err = si + N + 1;
+    // zero everything (pads of R/T, halos of U0/U1, state), then +inf in D
+    CK(cudaMemsetAsync(base, 0, L.total, st), "workspace clear");
+    CK(launch_fill(ws.D, INFINITY, (L.off_U0 - L.off_D) / 4, st), "distance halo fill");
+    return TNLM_OK;
+}
+
+tnlm_status check_geom_handle(const tnlm_geometry* g) {
+    if (!g) return fail(TNLM_ERR_INVALID_ARG, "geometry handle is NULL");
+    return TNLM_OK;
+}
+
+// One outer iteration of the TNLM algorithm box on the handle's workspace.
+tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f,
+                            cudaStream_t st) {
+    Workspace& ws = g->ws;
+    const size_t nps = (size_t)g->N * g->V * proj_chunks(g);
+    double* part_s = ws.part;
+    double* part_i = ws.part + nps;
+    // ---- data step: r0 = sqrt(w)(y - P f), s0 = P_n^T r0 (CGLS) / w(y - P f) back-projected (Eq. 4)
+    CK(launch_prep_dual(g, d_f, ws.R, ws.T, st), "prep");
+    CK(launch_copy(d_f, ws.u, (size_t)g->nx * g->ny * g->N, st), "copy");
+    ProjOut o{};
+    o.mode = 1; o.r = ws.r; o.z = ws.z; o.y = d_y; o.sw = ws.sw; o.part = part_s;
+    CK(launch_project(g, ws.R, ws.T, o, st), "project");
+    CK(launch_backproject(g, ws.z, ws.s, part_i, st), "backproject");
+    CK(launch_cgls_init_scalars(g, ws, st), "scalars");
+    if (p->data_step == TNLM_DATA_GRAD) {
+        CK(launch_grad_final(g, ws, p->beta, st), "gradient step");
+    } else {
+        for (int m = 0; m < p->m1; ++m) {
+            const bool last = m == p->m1 - 1;
+            CK(launch_prep_dual(g, ws.s, ws.R, ws.T, st), "prep");
+            ProjOut ot{};
+            ot.mode = 2; ot.q = ws.t; ot.sw = ws.sw; ot.part = part_s;
+            CK(launch_project(g, ws.R, ws.T, ot, st), "project");
+            CK(launch_cgls_a(g, ws, st), "cgls a");
+            CK(launch_cgls_update_ur(g, ws, !last, st), "cgls update");
+            if (last) break;
+            CK(launch_backproject(g, ws.z, ws.gr, part_i, st), "backproject");
+            CK(launch_cgls_b(g, ws, st), "cgls b");
+            CK(launch_cgls_update_s(g, ws, st), "cgls s");
+        }
+    }
+    // ---- TNLM step: weights from g = ws.u, Gauss-Jacobi, positivity
+    if (p->m2 > 0) {
+        CK(launch_weights(g, ws, p->patch, p->window, ws.u, st), "weights");
+        float* bufs[2] = {ws.U0, ws.U1};
+        for (int m = 0; m < p->m2; ++m) {
+            const bool last = m == p->m2 - 1;
+            CK(launch_gj_sweep(g, ws, p->window, p->h, p->mu_hat, ws.u, bufs[m & 1],
+                               last ? nullptr : bufs[(m + 1) & 1], last ? d_f : nullptr, p->clamp,
+                               st),
+               "gauss-jacobi");
+        }
+    } else {
+        CK(launch_finalize_nogj(g, ws, ws.u, d_f, p->clamp, st), "finalize");
+    }
+    CK(launch_iter_scalars(g, ws, gj_blocks(g), st), "monitors");
+    return TNLM_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* tnlm_last_error(void) { return g_err; }
+
+void tnlm_debug_fail_alloc_after(int n) { g_fail_after.store(n > 0 ? n : 0); }
+
+tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** out) {
+    g_err[0] = 0;
+    if (!out) return fail(TNLM_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!d) return fail(TNLM_ERR_INVALID_ARG, "desc is NULL");
+    if (d->nx < 1 || d->ny < 1 || d->nx > 8192 || d->ny > 8192)
+        return fail(TNLM_ERR_INVALID_ARG, "nx, ny must be in [1, 8192]");
+    if (d->n_phases < 3 || d->n_phases > 4096)
+        return fail(TNLM_ERR_INVALID_ARG, "n_phases must be in [3, 4096]");
+    if (d->n_views < 1 || d->n_bins < 1)
+        return fail(TNLM_ERR_INVALID_ARG, "n_views and n_bins must be >= 1");
+    if (d->n_bins > 4096) return fail(TNLM_ERR_INVALID_ARG, "n_bins must be <= 4096");
+    if ((long long)d->n_phases * d->n_views > 1000000)
+        return fail(TNLM_ERR_INVALID_ARG, "n_phases * n_views too large");
+    if (!(d->pixel_mm > 0) || !(d->bin_mm > 0) || !isfinite(d->pixel_mm) || !isfinite(d->bin_mm))
+        return fail(TNLM_ERR_INVALID_ARG, "pixel_mm and bin_mm must be finite and > 0");
+    const double half_diag = 0.5 * d->pixel_mm * sqrt((double)d->nx * d->nx + (double)d->ny * d->ny);
+    if (!(d->sid_mm > half_diag) || !isfinite(d->sid_mm))
+        return fail(TNLM_ERR_INVALID_ARG, "sid_mm must exceed the image half-diagonal %.3f mm", half_diag);
+    if (!(d->sdd_mm > d->sid_mm + half_diag) || !isfinite(d->sdd_mm))
+        return fail(TNLM_ERR_INVALID_ARG, "sdd_mm must exceed sid_mm + image half-diagonal");
+    if (d->detector != TNLM_DETECTOR_ARC) return fail(TNLM_ERR_INVALID_ARG, "only the arc detector is supported");
+    const double fan = 0.5 * d->n_bins * d->bin_mm / d->sdd_mm;
+    if (!(fan < 1.4)) return fail(TNLM_ERR_INVALID_ARG, "fan half-angle must be < 1.4 rad");
+    if (!d->view_angles_rad) return fail(TNLM_ERR_INVALID_ARG, "view_angles_rad is NULL");
+    const size_t NV = (size_t)d->n_phases * d->n_views;
+    for (size_t k = 0; k < NV; ++k)
+        if (!isfinite(d->view_angles_rad[k])) return fail(TNLM_ERR_INVALID_ARG, "non-finite view angle");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || d->device < 0 || d->device >= ndev) {
+        cudaGetLastError();
+        return fail(TNLM_ERR_INVALID_ARG, "device %d not available", d->device);
+    }
+    DeviceGuard dg(d->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+
+    tnlm_geometry* g = new tnlm_geometry();
+    g->device = d->device;
+    g->nx = d->nx; g->ny = d->ny; g->N = d->n_phases; g->V = d->n_views; g->B = d->n_bins;
+    g->pixel = d->pixel_mm; g->bin_mm = d->bin_mm; g->sid = d->sid_mm; g->sdd = d->sdd_mm;
+
+    // per-view (cos t, sin t), per-bin (cos g, sin g), per-ray chord constants (FP64 -> FP32)
+    std::vector<float2> hv(NV), hb(g->B);
+    std::vector<float4> hr(NV * g->B);
+    const double dg_ = g->bin_mm / g->sdd;
+    for (int b = 0; b < g->B; ++b) {
+        const double ga = (b - 0.5 * (g->B - 1)) * dg_;
+        hb[b] = make_float2((float)cos(ga), (float)sin(ga));
+    }
+    for (size_t v = 0; v < NV; ++v) {
+        const double t = d->view_angles_rad[v];
+        hv[v] = make_float2((float)cos(t), (float)sin(t));
+        for (int b = 0; b < g->B; ++b) {
+            const double phi = t + (b - 0.5 * (g->B - 1)) * dg_;
+            const double ax = fabs(cos(phi)), ay = fabs(sin(phi));
+            const double lo = fmax(fmin(ax, ay), 1e-30), hi = fmax(ax, ay);
+            hr[v * g->B + b] = make_float4((float)(0.5 * (ax + ay)), (float)(1.0 / lo),
+                                           (float)(1.0 / hi), 0.f);
+        }
+    }
+    void *pv = nullptr, *pb = nullptr, *pr = nullptr;
+    cudaError_t e = dev_alloc(&pv, sizeof(float2) * NV);
+    if (e == cudaSuccess) e = dev_alloc(&pb, sizeof(float2) * g->B);
+    if (e == cudaSuccess) e = dev_alloc(&pr, sizeof(float4) * NV * g->B);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(pv); cudaFree(pb); cudaFree(pr);
+        delete g;
+        return fail(e == cudaErrorMemoryAllocation ? TNLM_ERR_OOM : TNLM_ERR_CUDA,
+                    "geometry table allocation failed: %s", cudaGetErrorString(e));
+    }
+    g->d_view = (float2*)pv; g->d_bin = (float2*)pb; g->d_ray = (float4*)pr;
+    e = cudaMemcpy(pv, hv.data(), sizeof(float2) * NV, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pb, hb.data(), sizeof(float2) * g->B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pr, hr.data(), sizeof(float4) * NV * g->B, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        tnlm_destroy_geometry(g);
+        return cuda_fail(e, "geometry table upload");
+    }
+    *out = g;
+    return TNLM_OK;
+}
+
+void tnlm_destroy_geometry(tnlm_geometry* g) {
+    if (!g) return;
+    DeviceGuard dg(g->device);
+    cudaDeviceSynchronize();
+    cudaFree(g->d_view);
+    cudaFree(g->d_bin);
+    cudaFree(g->d_ray);
+    cudaFree(g->ws.base);
+    delete g;
+}
+
+tnlm_status tnlm_project(const tnlm_geometry* gc, const float* d_img, float* d_sino, void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    if (!d_img || !d_sino) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_img) || !aligned16(d_sino)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    tnlm_status s = ensure_ws(g, g->ws.base ? g->ws.rho : 0, g->ws.base ? g->ws.kcap : 1, st);
+    if (s != TNLM_OK) return s;
+    CK(launch_prep_dual(g, d_img, g->ws.R, g->ws.T, st), "prep");
+    ProjOut o{};
+    o.mode = 0; o.q = d_sino;
+    CK(launch_project(g, g->ws.R, g->ws.T, o, st), "project");
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_backproject(const tnlm_geometry* g, const float* d_sino, float* d_img, void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    if (!d_img || !d_sino) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_img) || !aligned16(d_sino)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    CK(launch_backproject(g, d_sino, d_img, nullptr, (cudaStream_t)stream), "backproject");
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_weights_size(const tnlm_geometry* g, const tnlm_params* p, size_t* dist_bytes,
+                              size_t* norm_bytes) {
+    g_err[0] = 0;
+    if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    tnlm_status s = check_params(p);
+    if (s != TNLM_OK) return s;
+    const size_t npx = (size_t)g->nx * g->ny * g->N;
+    if (dist_bytes) *dist_bytes = 4 * npx * p->window * p->window;
+    if (norm_bytes) *norm_bytes = 4 * 4 * npx;
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_workspace_bytes(const tnlm_geometry* g, const tnlm_params* p, size_t* bytes) {
+    g_err[0] = 0;
+    if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    tnlm_status s = check_params(p);
+    if (s != TNLM_OK) return s;
+    if (!bytes) return fail(TNLM_ERR_INVALID_ARG, "bytes is NULL");
+    *bytes = ws_layout(g, (p->window - 1) / 2, p->k_outer < 1 ? 1 : p->k_outer).total;
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_weights(const tnlm_geometry* gc, const tnlm_params* p, const float* d_g,
+                         float* d_dist, float* d_norm, void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    tnlm_status s = check_params(p);
+    if (s != TNLM_OK) return s;
+    if (!d_g || !d_dist || !d_norm) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_g) || !aligned16(d_dist) || !aligned16(d_norm))
+        return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    s = ensure_ws(g, (p->window - 1) / 2, g->ws.base ? g->ws.kcap : 1, st);
+    if (s != TNLM_OK) return s;
+    CK(launch_weights(g, g->ws, p->patch, p->window, d_g, st), "weights");
+    CK(launch_weights_norm(g, g->ws, p->window, p->h, st), "weights normalisers");
+    CK(launch_weights_export(g, g->ws, p->window, d_dist, d_norm, st), "weights export");
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_reconstruct(const tnlm_geometry* gc, const tnlm_params* p, const float* d_y,
+                             const float* d_winv, float* d_f, tnlm_report* rep, void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    tnlm_status s = check_params(p);
+    if (s != TNLM_OK) return s;
+    if (!d_y || !d_winv || !d_f) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_y) || !aligned16(d_winv) || !aligned16(d_f))
+        return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    s = ensure_ws(g, (p->window - 1) / 2, p->k_outer < 1 ? 1 : p->k_outer, st);
+    if (s != TNLM_OK) return s;
+    Workspace& ws = g->ws;
+    const size_t nsg = (size_t)g->N * g->V * g->B;
+    CK(cudaMemsetAsync(ws.st.iter, 0, sizeof(int), st), "reset");
+    CK(launch_sqrt(d_winv, ws.sw, nsg, ws.st.err, st), "sqrt");
+    const bool sync = rep != nullptr || p->tol > 0.0;
+    int done = 0;
+    for (int k = 0; k < p->k_outer; ++k) {
+        s = outer_iteration(g, p, d_y, d_f, st);
+        if (s != TNLM_OK) return s;
+        done = k + 1;
+        if (p->tol > 0.0 && (done % p->tol_check_every == 0 || done == p->k_outer)) {
+            double rel = 0.0;
+            CK(cudaMemcpyAsync(&rel, ws.st.hist_rel + k, sizeof(double), cudaMemcpyDeviceToHost, st),
+               "readback");
+            CK(cudaStreamSynchronize(st), "sync");
+            if (rel < p->tol) break;
+        }
+    }
+    if (sync) {
+        int err = 0;
+        CK(cudaMemcpyAsync(&err, ws.st.err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+        std::vector<double> hrel(done > 0 ? done : 1), hres(done > 0 ? done : 1);
+        if (done > 0) {
+            CK(cudaMemcpyAsync(hrel.data(), ws.st.hist_rel, sizeof(double) * done,
+                               cudaMemcpyDeviceToHost, st), "readback");
+            CK(cudaMemcpyAsync(hres.data(), ws.st.hist_res, sizeof(double) * done,
+                               cudaMemcpyDeviceToHost, st), "readback");
+        }
+        CK(cudaStreamSynchronize(st), "sync");
+        if (rep) {
+            rep->iterations = done;
+            rep->rel_change = done > 0 ? hrel[done - 1] : 0.0;
+            rep->data_residual = done > 0 ? hres[done - 1] : 0.0;
+            for (int k = 0; k < done; ++k) {
+                if (rep->rel_change_hist) rep->rel_change_hist[k] = hrel[k];
+                if (rep->residual_hist) rep->residual_hist[k] = hres[k];
+            }
+        }
+        if (err) {
+            CK(cudaMemsetAsync(ws.st.err, 0, sizeof(int), st), "reset");
+            return fail(TNLM_ERR_NUMERIC, "non-finite value met on the device (flags 0x%x)", err);
+        }
+    }
+    return TNLM_OK;
+}
+
+}  // extern "C"

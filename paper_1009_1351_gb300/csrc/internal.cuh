@@ -1,0 +1,169 @@
+// Internal declarations of the TNLM CUDA library (not part of the ABI).
+//
+// Data layout in HBM (per geometry handle; N phases, image nx x ny, V views,
+// B bins, window W = 2*rho+1):
+//   images        [N][ny][nx]             f, u (CGLS iterate / g), s, grad
+//   dual layout   R [N][ny][nx+4], T [N][nx][ny+4]: the projector's input in
+//                 row-major and column-major form with two zero pad lines on
+//                 each side, so that every ray reads consecutive addresses
+//                 across a warp whichever axis it marches along.
+//   sinograms     [N][V][B]               r, z = sqrt(w) r, t, sqrt(w)
+//   D planes      [N pairs][W*W][py][px]  patch distances of pair (i, i+1)
+//                 with a halo of rho rows and ox >= rho columns holding +inf
+//   u ping-pong   2 x [N][py][px]         Gauss-Jacobi iterates, zero halo
+//   minima        [2][N][ny][nx]          row minima of D per direction
+//   partials      FP64 per-block sums, reduced in a fixed order (deterministic)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "tnlm.h"
+
+namespace tnlm {
+
+constexpr int kMaxPatch = 15;
+constexpr int kMaxWindow = 31;
+constexpr int kProjThreads = 256;     // rays per projector block (one view)
+constexpr int kBpTile = 16;           // gather backprojector: 16 x 16 pixels per block
+constexpr int kWTileX = 32, kWTileY = 16;  // weight kernel output tile
+constexpr int kGjTileX = 32, kGjTileY = 8; // Gauss-Jacobi tile
+
+struct PadPlane {
+    int px, py;   // pitch (floats) and rows
+    int ox, oy;   // interior origin
+    size_t plane; // px * py
+};
+
+// Per-phase scalars of the data step and the per-iteration monitors.
+struct DevState {
+    double* gamma;     // [N] ||P_n^T r||^2 of the current CGLS step
+    double* a;         // [N]
+    double* b;         // [N]
+    double* res0;      // [N] ||r^(0)||^2 (data term of f^(k-1))
+    int* active;       // [N] CGLS not stopped
+    double* hist_rel;  // [kcap]
+    double* hist_res;  // [kcap]
+    int* iter;         // outer iteration counter (device)
+    int* err;          // numeric fault flag
+};
+
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+    int rho = -1;      // window radius the buffers are sized for
+    int kcap = 0;      // history capacity
+    // images
+    float *u = nullptr, *s = nullptr, *gr = nullptr;
+    float *R = nullptr, *T = nullptr;
+    // sinograms
+    float *r = nullptr, *z = nullptr, *t = nullptr, *sw = nullptr;
+    // TNLM step
+    PadPlane pp{};
+    float* D = nullptr;      // [N][W*W][py][px]
+    float* U0 = nullptr;     // [N][py][px]
+    float* U1 = nullptr;
+    float* mins = nullptr;   // [2][N][ny][nx]  (next, prev)
+    float* zn = nullptr;     // [2][N][ny][nx]  normalisers (public weights call only)
+    // reductions
+    double* part = nullptr;  // partial sums
+    size_t part_len = 0;
+    double* part2 = nullptr; // second partial array (relative change)
+    DevState st{};
+};
+
+}  // namespace tnlm
+
+struct tnlm_geometry {
+    int device;
+    int nx, ny, N, V, B;
+    double pixel, bin_mm, sid, sdd;
+    float2* d_view = nullptr;   // [N*V] (cos t, sin t)
+    float2* d_bin = nullptr;    // [B] (cos g, sin g)
+    float4* d_ray = nullptr;    // [N*V*B] (ab2, 1/min(|ux|,|uy|), 1/max(|ux|,|uy|), 0)
+    tnlm::Workspace ws;
+};
+
+namespace tnlm {
+
+// ---- launchers (defined in the .cu files) --------------------------------
+struct ProjOut {
+    int mode;              // 0: q, 1: r = sw (y - q), z = sw r, 2: t = sw q
+    float* q;              // mode 0 output / mode 2 t
+    float* r;              // mode 1
+    float* z;              // mode 1
+    const float* y;        // mode 1
+    const float* sw;       // modes 1, 2
+    double* part;          // modes 1, 2: [N*V*nchunk] partial sums of squares
+};
+int proj_chunks(const tnlm_geometry* g);
+cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R, float* T,
+                             cudaStream_t st);
+cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
+                           const ProjOut& o, cudaStream_t st);
+int bp_blocks_per_phase(const tnlm_geometry* g);
+cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float* img,
+                               double* part, cudaStream_t st);
+
+// CGLS vector / scalar kernels
+cudaError_t launch_cgls_init_scalars(const tnlm_geometry* g, const Workspace& ws,
+                                     cudaStream_t st);
+cudaError_t launch_cgls_a(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st);
+cudaError_t launch_cgls_update_ur(const tnlm_geometry* g, const Workspace& ws, bool with_r,
+                                  cudaStream_t st);
+cudaError_t launch_cgls_b(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st);
+cudaError_t launch_cgls_update_s(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st);
+cudaError_t launch_grad_final(const tnlm_geometry* g, const Workspace& ws, double beta,
+                              cudaStream_t st);
+cudaError_t launch_sqrt(const float* w, float* sw, size_t n, int* err, cudaStream_t st);
+cudaError_t launch_copy(const float* src, float* dst, size_t n, cudaStream_t st);
+cudaError_t launch_fill(float* p, float v, size_t n, cudaStream_t st);
+
+// TNLM step kernels
+cudaError_t launch_weights(const tnlm_geometry* g, const Workspace& ws, int patch, int window,
+                           const float* gimg, cudaStream_t st);
+cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int window, double h,
+                            double mu_hat, const float* gimg, const float* uin, float* uout,
+                            float* fout, int clamp, cudaStream_t st);
+cudaError_t launch_finalize_nogj(const tnlm_geometry* g, const Workspace& ws, const float* gimg,
+                                 float* fout, int clamp, cudaStream_t st);
+cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks,
+                                cudaStream_t st);
+int gj_blocks(const tnlm_geometry* g);
+cudaError_t launch_weights_norm(const tnlm_geometry* g, const Workspace& ws, int window,
+                                double h, cudaStream_t st);
+cudaError_t launch_weights_export(const tnlm_geometry* g, const Workspace& ws, int window,
+                                  float* d_dist, float* d_norm, cudaStream_t st);
+
+// ---- device helpers -------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block reduction: each warp reduces in FP32 (a depth-5 tree), warp totals
+// are combined in FP64 in warp order by thread 0.  Deterministic.
+template <int NT>
+__device__ __forceinline__ double block_sum(float v, double* sh, int tid) {
+    v = warp_sum(v);
+    const int lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) sh[wid] = (double)v;
+    __syncthreads();
+    double tot = 0.0;
+    if (tid == 0) {
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) tot += sh[k];
+    }
+    __syncthreads();
+    return tot;
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+}  // namespace tnlm

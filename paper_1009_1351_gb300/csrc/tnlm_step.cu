@@ -1,0 +1,406 @@
+// TNLM step (Sec. 2.2-2.3): Eq. 8 weights from g^(k), then M2 Gauss-Jacobi
+// sweeps of Eq. 7, then the positivity truncation.
+//
+// K4 (k_weights) computes, for each cyclic pair (i, i+1) and every pixel x
+// and shift s of the W x W window, the patch distance
+//   D_i(x, s) = sum_{|p|<=r} (g_i(x+p) - g_{i+1}(x+s+p))^2   (zero outside the image)
+// once, and stores it in a single array that both directions read (the
+// symmetric reuse of Sec. 2.3: omega_{i,i+1}(x, x+s) and omega_{i+1,i}(x+s, x)
+// share exp(-D/h^2) before normalisation).  Eq. 8 is evaluated as a stable
+// softmax, exp(-(D - m)/h^2) / Z with m the row minimum; K4 also produces m
+// for both directions:
+//   m_next_i(x)     = min_s D_i(x, s)            (row x of phase i toward i+1)
+//   m_prev_{i+1}(y) = min_s D_i(y - s, s)        (row y of phase i+1 toward i)
+// A block owns a 32 x 16 tile T of one pair.  For each shift it forms the
+// horizontal patch sums over the bounding box of T and T - s (staged in
+// shared memory), then each thread sums them vertically for its own pixel
+// (forward row) and for the pixel it receives from (backward row).
+//
+// K5 (k_gj) is one Gauss-Jacobi sweep, one thread per pixel of one phase.  It
+// streams the two distance planes that touch phase i (pair i forward at x,
+// pair i-1 backward at x - s) and forms both normalisers on the fly:
+//   u_i^+(x) = g_i(x)/(mu+1) + mu/(2mu+2) [ sum_s e_p u_{i-1}(x-s) / sum_s e_p
+//                                         + sum_s e_n u_{i+1}(x+s) / sum_s e_n ]
+// with e = 2^(log2(e) (m - D) / h^2).  Blocks are ordered tile-major, phase-
+// minor, so the two reads of a distance plane (by phase i and phase i+1)
+// happen close together in time and the second is served from L2.
+#include "internal.cuh"
+
+#include <math.h>
+
+namespace tnlm {
+
+struct WArgs {
+    const float* g;
+    float* D;
+    float* mins;
+    float* U0;
+    int* err;
+    PadPlane pp;
+    int nx, ny, N, rho, W;
+};
+
+template <int R>
+__global__ void __launch_bounds__(256) k_weights(WArgs a) {
+    extern __shared__ float sm[];
+    const int rho = a.rho, W = a.W;
+    const int GW = kWTileX + 2 * (rho + R), GH = kWTileY + 2 * (rho + R);
+    const int HW = kWTileX + rho, HH = kWTileY + rho + 2 * R;
+    float* Gi = sm;
+    float* Gj = Gi + GW * GH;
+    float* Hb = Gj + GW * GH;
+    const int p = blockIdx.z, j = (p + 1) % a.N;
+    const int X0 = blockIdx.x * kWTileX, Y0 = blockIdx.y * kWTileY;
+    const int gx0 = X0 - rho - R, gy0 = Y0 - rho - R;
+    const int tid = threadIdx.x;
+    const int nx = a.nx, ny = a.ny;
+    const size_t npx = (size_t)nx * ny;
+    const float* gp = a.g + p * npx;
+    const float* gq = a.g + j * npx;
+    for (int e = tid; e < GW * GH; e += 256) {
+        const int x = gx0 + e % GW, y = gy0 + e / GW;
+        const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
+        Gi[e] = in ? gp[(size_t)y * nx + x] : 0.f;
+        Gj[e] = in ? gq[(size_t)y * nx + x] : 0.f;
+    }
+    const int tx = tid & 31, ty = tid >> 5;
+    if (a.U0) {  // padded copy of g_p: u^(0) of the Gauss-Jacobi sweeps
+        for (int kk = 0; kk < 2; ++kk) {
+            const int x = X0 + tx, y = Y0 + ty + 8 * kk;
+            if (x < nx && y < ny)
+                a.U0[p * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] =
+                    gp[(size_t)y * nx + x];
+        }
+    }
+    __syncthreads();
+
+    float mf[2] = {INFINITY, INFINITY}, mb[2] = {INFINITY, INFINITY};
+    const size_t W2 = (size_t)W * W;
+    float* Dp = a.D + (size_t)p * W2 * a.pp.plane;
+    for (int sy = -rho; sy <= rho; ++sy) {
+        for (int sx = -rho; sx <= rho; ++sx) {
+            const int k = (sy + rho) * W + (sx + rho);
+            float* H = Hb + (k & 1) * HW * HH;
+            const int bw = kWTileX + abs(sx), bh = kWTileY + abs(sy);
+            const int ox = X0 + min(0, -sx), oy = Y0 + min(0, -sy);
+            const int nrow = bh + 2 * R;
+            // horizontal patch sums over the box, rows widened by r
+            for (int e = tid; e < bw * nrow; e += 256) {
+                const int cx = e % bw, cr = e / bw;
+                const int zx = ox + cx, zy = oy + cr - R;
+                const float* pi = Gi + (zy - gy0) * GW + (zx - gx0);
+                const float* pj = Gj + (zy + sy - gy0) * GW + (zx + sx - gx0);
+                float h = 0.f;
+#pragma unroll
+                for (int q = -R; q <= R; ++q) {
+                    const float d = pi[q] - pj[q];
+                    h = fmaf(d, d, h);
+                }
+                H[cr * HW + cx] = h;
+            }
+            __syncthreads();
+            // vertical sums for this thread's pixels: forward (x) and backward (x - s)
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const int x = X0 + tx, y = Y0 + ty + 8 * kk;
+                const bool in = x < nx && y < ny;
+                {
+                    const int cx = x - ox, cr = y - oy;
+                    float d = 0.f;
+#pragma unroll
+                    for (int q = 0; q <= 2 * R; ++q) d += H[(cr + q) * HW + cx];
+                    const bool valid = in && x + sx >= 0 && x + sx < nx && y + sy >= 0 && y + sy < ny;
+                    if (in)
+                        Dp[(size_t)k * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] =
+                            valid ? d : INFINITY;
+                    if (valid) mf[kk] = fminf(mf[kk], d);
+                }
+                {
+                    const int cx = x - sx - ox, cr = y - sy - oy;
+                    float d = 0.f;
+#pragma unroll
+                    for (int q = 0; q <= 2 * R; ++q) d += H[(cr + q) * HW + cx];
+                    const bool valid = in && x - sx >= 0 && x - sx < nx && y - sy >= 0 && y - sy < ny;
+                    if (valid) mb[kk] = fminf(mb[kk], d);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 2; ++kk) {
+        const int x = X0 + tx, y = Y0 + ty + 8 * kk;
+        if (x < nx && y < ny) {
+            const size_t pix = (size_t)y * nx + x;
+            a.mins[p * npx + pix] = mf[kk];                        // m_next of phase p
+            a.mins[(size_t)(a.N + j) * npx + pix] = mb[kk];        // m_prev of phase p+1
+            if (!(mf[kk] < INFINITY) || !(mb[kk] < INFINITY)) atomicOr(a.err, 4);
+        }
+    }
+}
+
+static size_t weights_smem(int rho, int R) {
+    const int GW = kWTileX + 2 * (rho + R), GH = kWTileY + 2 * (rho + R);
+    const int HW = kWTileX + rho, HH = kWTileY + rho + 2 * R;
+    return sizeof(float) * (2 * (size_t)GW * GH + 2 * (size_t)HW * HH);
+}
+
+template <int R>
+static cudaError_t launch_weights_r(const WArgs& a, cudaStream_t st) {
+    const size_t smem = weights_smem(a.rho, R);
+    cudaError_t e = cudaFuncSetAttribute(k_weights<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.nx + kWTileX - 1) / kWTileX, (a.ny + kWTileY - 1) / kWTileY, a.N);
+    k_weights<R><<<grid, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights(const tnlm_geometry* g, const Workspace& ws, int patch, int window,
+                           const float* gimg, cudaStream_t st) {
+    WArgs a;
+    a.g = gimg; a.D = ws.D; a.mins = ws.mins; a.U0 = ws.U0; a.err = ws.st.err; a.pp = ws.pp;
+    a.nx = g->nx; a.ny = g->ny; a.N = g->N; a.rho = (window - 1) / 2; a.W = window;
+    switch ((patch - 1) / 2) {
+        case 0: return launch_weights_r<0>(a, st);
+        case 1: return launch_weights_r<1>(a, st);
+        case 2: return launch_weights_r<2>(a, st);
+        case 3: return launch_weights_r<3>(a, st);
+        case 4: return launch_weights_r<4>(a, st);
+        case 5: return launch_weights_r<5>(a, st);
+        case 6: return launch_weights_r<6>(a, st);
+        case 7: return launch_weights_r<7>(a, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K5
+// ---------------------------------------------------------------------------
+struct GjArgs {
+    const float* D;
+    const float* mins;
+    const float* g;
+    const float* uin;
+    float* uout;
+    float* fout;
+    float* zn;
+    double* part;
+    int* err;
+    PadPlane pp;
+    int nx, ny, N, rho, W, clamp;
+    float k2, c1, c2;
+};
+
+// MODE 0: intermediate sweep (uout, padded); 1: last sweep, clamp, write f and
+// the relative-change partials; 2: write the normalisers Z (public weights).
+template <int MODE>
+__global__ void __launch_bounds__(kGjTileX * kGjTileY) k_gj(GjArgs a) {
+    const int N = a.N, nx = a.nx, ny = a.ny;
+    const int tile = blockIdx.x / N, i = blockIdx.x % N;
+    const int tilesx = (nx + kGjTileX - 1) / kGjTileX;
+    const int tid = threadIdx.x;
+    const int x = (tile % tilesx) * kGjTileX + (tid & 31);
+    const int y = (tile / tilesx) * kGjTileY + (tid >> 5);
+    const bool in = x < nx && y < ny;
+    const size_t npx = (size_t)nx * ny;
+    const int ip = (i + N - 1) % N, inx = (i + 1) % N;
+    float af = 0.f, zf = 0.f, ab = 0.f, zb = 0.f;
+    const size_t pix = (size_t)y * nx + x;
+    if (in) {
+        const int rho = a.rho, W = a.W, px = a.pp.px;
+        const size_t plane = a.pp.plane, W2 = (size_t)W * W;
+        const float k2 = a.k2;
+        const float mfk = a.mins[i * npx + pix] * k2;
+        const float mbk = a.mins[(N + i) * npx + pix] * k2;
+        const size_t cpos = (size_t)(y + a.pp.oy) * px + x + a.pp.ox;
+        const float* dn = a.D + (size_t)i * W2 * plane + cpos;
+        const float* dp = a.D + (size_t)ip * W2 * plane + cpos + (size_t)rho * px + rho;
+        const float* un = a.uin + inx * plane + cpos - (size_t)rho * px - rho;
+        const float* up = a.uin + ip * plane + cpos + (size_t)rho * px + rho;
+        for (int sy = 0; sy < W; ++sy) {
+            const float* dnr = dn + (size_t)sy * W * plane;
+            const float* dpr = dp + (size_t)sy * W * plane - (size_t)sy * px;
+            const float* unr = un + (size_t)sy * px;
+            const float* upr = up - (size_t)sy * px;
+#pragma unroll 4
+            for (int sx = 0; sx < W; ++sx) {
+                const float Df = __ldg(dnr + (size_t)sx * plane);
+                const float Db = __ldg(dpr + (size_t)sx * plane - sx);
+                const float ef = ex2_approx(fmaf(-Df, k2, mfk));
+                const float eb = ex2_approx(fmaf(-Db, k2, mbk));
+                if (MODE != 2) {
+                    af = fmaf(ef, __ldg(unr + sx), af);
+                    ab = fmaf(eb, __ldg(upr - sx), ab);
+                }
+                zf += ef;
+                zb += eb;
+            }
+        }
+        if (!(zf >= 1.f) || !(zb >= 1.f)) atomicOr(a.err, 8);
+    }
+    if (MODE == 2) {
+        if (in) {
+            a.zn[i * npx + pix] = zf;
+            a.zn[(N + i) * npx + pix] = zb;
+        }
+        return;
+    }
+    const float unew = in ? fmaf(a.g[i * npx + pix], a.c1, a.c2 * (af / zf + ab / zb)) : 0.f;
+    if (MODE == 0) {
+        if (in) a.uout[i * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] = unew;
+        return;
+    }
+    float fnew = 0.f, dif = 0.f;
+    if (in) {
+        fnew = a.clamp ? fmaxf(unew, 0.f) : unew;
+        const float fold = a.fout[i * npx + pix];
+        a.fout[i * npx + pix] = fnew;
+        dif = fnew - fold;
+    }
+    __shared__ double sh[kGjTileX * kGjTileY / 32];
+    const double d2 = block_sum<kGjTileX * kGjTileY>(dif * dif, sh, tid);
+    const double n2 = block_sum<kGjTileX * kGjTileY>(fnew * fnew, sh, tid);
+    if (tid == 0) {
+        a.part[2 * (size_t)blockIdx.x] = d2;
+        a.part[2 * (size_t)blockIdx.x + 1] = n2;
+    }
+}
+
+int gj_blocks(const tnlm_geometry* g) {
+    return ((g->nx + kGjTileX - 1) / kGjTileX) * ((g->ny + kGjTileY - 1) / kGjTileY) * g->N;
+}
+
+static GjArgs gj_args(const tnlm_geometry* g, const Workspace& ws, int window, double h,
+                      double mu_hat) {
+    GjArgs a;
+    a.D = ws.D; a.mins = ws.mins; a.g = nullptr; a.uin = nullptr; a.uout = nullptr;
+    a.fout = nullptr; a.zn = ws.zn; a.part = ws.part2; a.err = ws.st.err; a.pp = ws.pp;
+    a.nx = g->nx; a.ny = g->ny; a.N = g->N; a.rho = (window - 1) / 2; a.W = window; a.clamp = 0;
+    a.k2 = (float)(1.4426950408889634 / (h * h));
+    a.c1 = (float)(1.0 / (mu_hat + 1.0));
+    a.c2 = (float)(mu_hat / (2.0 * mu_hat + 2.0));
+    return a;
+}
+
+cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int window, double h,
+                            double mu_hat, const float* gimg, const float* uin, float* uout,
+                            float* fout, int clamp, cudaStream_t st) {
+    GjArgs a = gj_args(g, ws, window, h, mu_hat);
+    a.g = gimg; a.uin = uin; a.uout = uout; a.fout = fout; a.clamp = clamp;
+    const int nb = gj_blocks(g);
+    if (fout)
+        k_gj<1><<<nb, kGjTileX * kGjTileY, 0, st>>>(a);
+    else
+        k_gj<0><<<nb, kGjTileX * kGjTileY, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights_norm(const tnlm_geometry* g, const Workspace& ws, int window, double h,
+                                cudaStream_t st) {
+    GjArgs a = gj_args(g, ws, window, h, 0.0);
+    a.uin = ws.U0;
+    k_gj<2><<<gj_blocks(g), kGjTileX * kGjTileY, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+// M2 = 0: f = max(g, 0) (or g), with the relative-change partials.
+__global__ void __launch_bounds__(256) k_finalize_nogj(const float* __restrict__ gimg,
+                                                       float* __restrict__ fout, double* part,
+                                                       int nx, int ny, int N, int clamp) {
+    const int tile = blockIdx.x / N, i = blockIdx.x % N;
+    const int tilesx = (nx + kGjTileX - 1) / kGjTileX;
+    const int tid = threadIdx.x;
+    const int x = (tile % tilesx) * kGjTileX + (tid & 31);
+    const int y = (tile / tilesx) * kGjTileY + (tid >> 5);
+    const size_t npx = (size_t)nx * ny;
+    float fnew = 0.f, dif = 0.f;
+    if (x < nx && y < ny) {
+        const size_t k = i * npx + (size_t)y * nx + x;
+        const float v = gimg[k];
+        fnew = clamp ? fmaxf(v, 0.f) : v;
+        dif = fnew - fout[k];
+        fout[k] = fnew;
+    }
+    __shared__ double sh[8];
+    const double d2 = block_sum<256>(dif * dif, sh, tid);
+    const double n2 = block_sum<256>(fnew * fnew, sh, tid);
+    if (tid == 0) {
+        part[2 * (size_t)blockIdx.x] = d2;
+        part[2 * (size_t)blockIdx.x + 1] = n2;
+    }
+}
+
+cudaError_t launch_finalize_nogj(const tnlm_geometry* g, const Workspace& ws, const float* gimg,
+                                 float* fout, int clamp, cudaStream_t st) {
+    k_finalize_nogj<<<gj_blocks(g), 256, 0, st>>>(gimg, fout, ws.part2, g->nx, g->ny, g->N, clamp);
+    return cudaGetLastError();
+}
+
+// Per-iteration monitors: relative change and the data term of f^(k-1).
+__global__ void k_iter_scalars(const double* part, int nblocks, const double* res0, int N,
+                               DevState st, int kcap) {
+    double d = 0.0, n = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += 32) {
+        d += part[2 * (size_t)k];
+        n += part[2 * (size_t)k + 1];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        d += __shfl_down_sync(0xffffffffu, d, o);
+        n += __shfl_down_sync(0xffffffffu, n, o);
+    }
+    if (threadIdx.x == 0) {
+        double r = 0.0;
+        for (int i = 0; i < N; ++i) r += res0[i];
+        const int it = *st.iter;
+        if (it < kcap) {
+            st.hist_rel[it] = n > 0.0 ? sqrt(d / n) : 0.0;
+            st.hist_res[it] = r;
+        }
+        *st.iter = it + 1;
+    }
+}
+
+cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks,
+                                cudaStream_t st) {
+    k_iter_scalars<<<1, 32, 0, st>>>(ws.part2, nblocks, ws.st.res0, g->N, ws.st, ws.kcap);
+    return cudaGetLastError();
+}
+
+// Public weights output: D to [N][W*W][ny][nx], (m, Z) to [4][N][ny][nx].
+__global__ void __launch_bounds__(256) k_weights_export(const float* __restrict__ D,
+                                                        const float* __restrict__ mins,
+                                                        const float* __restrict__ zn,
+                                                        float* __restrict__ dist,
+                                                        float* __restrict__ norm, PadPlane pp,
+                                                        int nx, int ny, int N, int W2) {
+    const size_t npx = (size_t)nx * ny;
+    const size_t nd = npx * N * W2;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < nd + 4 * npx * N;
+         k += stride) {
+        if (k < nd) {
+            const size_t pl = k / npx, pix = k % npx;
+            const int y = (int)(pix / nx), x = (int)(pix % nx);
+            dist[k] = D[pl * pp.plane + (size_t)(y + pp.oy) * pp.px + x + pp.ox];
+        } else {
+            const size_t q = k - nd;
+            const int c = (int)(q / (npx * N));
+            const size_t r = q % (npx * N);
+            // c: 0 m_next, 1 Z_next, 2 m_prev, 3 Z_prev
+            norm[q] = (c & 1) ? zn[(size_t)(c >> 1) * npx * N + r] : mins[(size_t)(c >> 1) * npx * N + r];
+        }
+    }
+}
+
+cudaError_t launch_weights_export(const tnlm_geometry* g, const Workspace& ws, int window,
+                                  float* d_dist, float* d_norm, cudaStream_t st) {
+    const size_t n = (size_t)g->nx * g->ny * g->N * (window * window + 4);
+    size_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    k_weights_export<<<(int)b, 256, 0, st>>>(ws.D, ws.mins, ws.zn, d_dist, d_norm, ws.pp, g->nx,
+                                             g->ny, g->N, window * window);
+    return cudaGetLastError();
+}
+
+}  // namespace tnlm

@@ -1,0 +1,96 @@
+"""Failure handling of the C ABI on a GPU, all provoked from the host:
+bad arguments, an injected allocation failure, non-finite inputs.  No test
+here makes a kernel fault, trap or wait."""
+import numpy as np
+import pytest
+
+from paper_1009_1351_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import paper_1009_1351_gb300 as tn
+    from paper_1009_1351_gb300 import build
+    build.build()
+    tn.load_library()
+    return tn
+
+
+@pytest.fixture(scope="module")
+def case():
+    c = synth.case("tiny")
+    d = synth.make_inputs(c)
+    dv = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
+    return c, dv(d["y"]), dv(d["w"]), dv(np.full((10, 64, 64), 0.01))
+
+
+@pytest.mark.parametrize("bad", [dict(patch=4), dict(patch=17), dict(window=33), dict(window=0),
+                                 dict(h=0.0), dict(h=float("nan")), dict(mu_hat=-1.0),
+                                 dict(data_step=2), dict(data_step=1, beta=0.0), dict(m1=-1),
+                                 dict(clamp=2)])
+def test_invalid_params_are_rejected(tn, case, bad):
+    c, y, w, f0 = case
+    geo = tn.tnlm_create_geometry(c.geom)
+    p = synth.Params(**{**c.params.__dict__, **bad})
+    f = f0.clone()
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_reconstruct(geo, p, y, w, f)
+    assert e.value.status == tn.TNLM_ERR_INVALID_ARG
+    assert torch.equal(f, f0)
+
+
+def test_misaligned_pointer_is_rejected(tn, case):
+    c, y, w, f0 = case
+    geo = tn.tnlm_create_geometry(c.geom)
+    big = torch.zeros(f0.numel() + 4, device="cuda")
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_reconstruct(geo, c.params, y, w, big.data_ptr() + 4)
+    assert e.value.status == tn.TNLM_ERR_INVALID_ARG
+
+
+def test_injected_allocation_failure_reports_oom_and_recovers(tn, case):
+    c, y, w, f0 = case
+    p = synth.Params(**{**c.params.__dict__, "k_outer": 2})
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    tn.tnlm_debug_fail_alloc_after(1)          # the geometry's first table
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_create_geometry(c.geom)
+    assert e.value.status == tn.TNLM_ERR_OOM
+    geo = tn.tnlm_create_geometry(c.geom)
+    tn.tnlm_debug_fail_alloc_after(1)          # the workspace
+    f = f0.clone()
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_reconstruct(geo, p, y, w, f)
+    assert e.value.status == tn.TNLM_ERR_OOM
+    assert torch.equal(f, f0)
+    tn.tnlm_reconstruct(geo, p, y, w, f)       # works afterwards
+    geo2 = tn.tnlm_create_geometry(c.geom)
+    f2 = f0.clone()
+    tn.tnlm_reconstruct(geo2, p, y, w, f2)
+    assert torch.equal(f, f2)
+    geo.close()
+    geo2.close()
+    torch.cuda.synchronize()
+    assert abs(torch.cuda.mem_get_info()[0] - free0) < (4 << 20)
+
+
+def test_nonfinite_input_raises_numeric(tn, case):
+    c, y, w, f0 = case
+    geo = tn.tnlm_create_geometry(c.geom)
+    p = synth.Params(**{**c.params.__dict__, "k_outer": 1})
+    ybad = y.clone()
+    ybad[3, 10, 20] = float("nan")
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_reconstruct(geo, p, ybad, w, f0.clone())
+    assert e.value.status == tn.TNLM_ERR_NUMERIC
+    wbad = w.clone()
+    wbad[0, 0, 0] = -1.0
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_reconstruct(geo, p, y, wbad, f0.clone())
+    assert e.value.status == tn.TNLM_ERR_NUMERIC
+    # the flag is cleared once reported
+    tn.tnlm_reconstruct(geo, p, y, w, f0.clone())
