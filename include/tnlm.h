@@ -161,6 +161,29 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* geom, const tnlm_params* param
                              const float* d_y, const float* d_winv, float* d_f,
                              tnlm_report* rep, void* stream);
 
+/* Kernel classes, for launch counting and optional device timing. */
+enum {
+    TNLM_KCLASS_PREP = 0,        /* layout copies, fills, sqrt(Sigma^{-1}) */
+    TNLM_KCLASS_PROJECT = 1,     /* P (forward projection) */
+    TNLM_KCLASS_BACKPROJECT = 2, /* P^T (gather backprojection) */
+    TNLM_KCLASS_CGLS = 3,        /* CGLS / Eq. 4 vector updates, FP64 scalar and monitor kernels */
+    TNLM_KCLASS_WEIGHTS = 4,     /* Eq. 8 patch distances, normalisers, export */
+    TNLM_KCLASS_GJ = 5,          /* Gauss-Jacobi sweeps (and the M2 = 0 finalisation) */
+    TNLM_KCLASS_COUNT = 6
+};
+
+/* Profiling (tracing) of the handle's kernels.  Launches of every class are
+ * always counted on the host.  Classes in class_mask (bit c = class c) are
+ * additionally bracketed by CUDA events recorded on the launch stream, so
+ * their device time can be read back; 0 turns the timing off.  Timing adds
+ * two event records per timed launch. */
+tnlm_status tnlm_profile_enable(tnlm_geometry* geom, unsigned int class_mask);
+
+/* ms[TNLM_KCLASS_COUNT]: summed device time (ms) of the timed launches per
+ * class; launches[TNLM_KCLASS_COUNT]: launches per class; either may be NULL.
+ * Synchronises the handle's device.  reset != 0 clears both afterwards. */
+tnlm_status tnlm_profile_read(tnlm_geometry* geom, double* ms, long long* launches, int reset);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char* tnlm_last_error(void);
 

@@ -28,7 +28,9 @@ TNLM_DATA_GRAD = 1
 
 EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tnlm_backproject",
             "tnlm_weights_size", "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct",
-            "tnlm_last_error", "tnlm_debug_fail_alloc_after")
+            "tnlm_last_error", "tnlm_debug_fail_alloc_after", "tnlm_profile_enable",
+            "tnlm_profile_read")
+KCLASSES = ("prep", "project", "backproject", "cgls", "weights", "gj")
 
 
 class GeometryDesc(ctypes.Structure):
@@ -86,8 +88,12 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_last_error.restype = ctypes.c_char_p
     lib.tnlm_debug_fail_alloc_after.argtypes = [ctypes.c_int]
     lib.tnlm_debug_fail_alloc_after.restype = None
+    lib.tnlm_profile_enable.argtypes = [vp, ctypes.c_uint]
+    lib.tnlm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
     for name in ("tnlm_create_geometry", "tnlm_project", "tnlm_backproject", "tnlm_weights_size",
-                 "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct"):
+                 "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct", "tnlm_profile_enable",
+                 "tnlm_profile_read"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -227,3 +233,20 @@ def tnlm_reconstruct(geom: Geometry, params, y, winv, f, report: bool = True,
 
 def tnlm_debug_fail_alloc_after(n: int) -> None:
     load_library().tnlm_debug_fail_alloc_after(int(n))
+
+
+def tnlm_profile_enable(geom: Geometry, classes=()) -> None:
+    """Time the launches of these kernel classes (names from KCLASSES) with
+    CUDA events on their stream; () turns timing off (counting stays on)."""
+    mask = 0
+    for c in classes:
+        mask |= 1 << KCLASSES.index(c)
+    _check(load_library().tnlm_profile_enable(geom.handle, mask))
+
+
+def tnlm_profile_read(geom: Geometry, reset: bool = True) -> Dict[str, Dict[str, float]]:
+    """{class: {"ms": device time of timed launches, "launches": count}}."""
+    ms = (ctypes.c_double * len(KCLASSES))()
+    n = (ctypes.c_longlong * len(KCLASSES))()
+    _check(load_library().tnlm_profile_read(geom.handle, ms, n, 1 if reset else 0))
+    return {c: {"ms": ms[k], "launches": int(n[k])} for k, c in enumerate(KCLASSES)}

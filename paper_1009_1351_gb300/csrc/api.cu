@@ -64,6 +64,53 @@ struct DeviceGuard {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Event pairs recorded around timed launches; reused after each read.
+struct Profiler {
+    std::vector<cudaEvent_t> ev;   // 2 per timed launch
+    std::vector<int> cls;          // class of each pair
+    size_t used = 0;               // pairs recorded since the last read
+};
+
+// Counts one launch of class c and, if c is timed, brackets it with events.
+struct LaunchScope {
+    tnlm_geometry* g;
+    int c;
+    cudaStream_t st;
+    cudaEvent_t end = nullptr;
+    LaunchScope(const tnlm_geometry* gc, int cls, cudaStream_t s)
+        : g(const_cast<tnlm_geometry*>(gc)), c(cls), st(s) {
+        g->launches[c]++;
+        if (!(g->prof_mask & (1u << c))) return;
+        Profiler* P = (Profiler*)g->prof;
+        if (!P) g->prof = P = new Profiler();
+        if (P->used * 2 + 2 > P->ev.size()) {
+            cudaEvent_t a, b;
+            if (cudaEventCreate(&a) != cudaSuccess) return;
+            if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+            P->ev.push_back(a);
+            P->ev.push_back(b);
+            P->cls.push_back(c);
+        }
+        P->cls[P->used] = c;
+        cudaEventRecord(P->ev[2 * P->used], st);
+        end = P->ev[2 * P->used + 1];
+        P->used++;
+    }
+    ~LaunchScope() {
+        if (end) cudaEventRecord(end, st);
+    }
+};
+
+#define LK(cls, call, what)                                     \
+    do {                                                        \
+        cudaError_t e_;                                         \
+        {                                                       \
+            LaunchScope ls_(g, cls, st);                        \
+            e_ = (call);                                        \
+        }                                                       \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);      \
+    } while (0)
+
 tnlm_status check_params(const tnlm_params* p) {
     if (!p) return fail(TNLM_ERR_INVALID_ARG, "params is NULL");
     if (!(p->mu_hat >= 0.0) || !isfinite(p->mu_hat))
@@ -102,10 +149,12 @@ WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
     WsLayout L{};
     const size_t npx = (size_t)g->nx * g->ny, N = g->N;
     const size_t nsg = (size_t)g->V * g->B;
-    const int ox = (int)align_up((size_t)rho, 4);
+    // interior starts at a 16-byte aligned column with one spare float4 beyond
+    // the window radius on each side (vectorised Gauss-Jacobi windows)
+    const int ox = (int)align_up((size_t)rho, 4) + 4;
     L.pp.ox = ox;
     L.pp.oy = rho;
-    L.pp.px = (int)align_up((size_t)g->nx + 2 * ox, 4);
+    L.pp.px = (int)align_up((size_t)g->nx, 4) + 2 * ox;
     L.pp.py = g->ny + 2 * rho;
     L.pp.plane = (size_t)L.pp.px * L.pp.py;
     const size_t W2 = (size_t)(2 * rho + 1) * (2 * rho + 1);
@@ -190,7 +239,7 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     ws.st.err = si + N + 1;
     // zero everything (pads of R/T, halos of U0/U1, state), then +inf in D
     CK(cudaMemsetAsync(base, 0, L.total, st), "workspace clear");
-    CK(launch_fill(ws.D, INFINITY, (L.off_U0 - L.off_D) / 4, st), "distance halo fill");
+    LK(TNLM_KCLASS_PREP, launch_fill(ws.D, INFINITY, (L.off_U0 - L.off_D) / 4, st), "distance halo fill");
     return TNLM_OK;
 }
 
@@ -207,45 +256,45 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     double* part_s = ws.part;
     double* part_i = ws.part + nps;
     // ---- data step: r0 = sqrt(w)(y - P f), s0 = P_n^T r0 (CGLS) / w(y - P f) back-projected (Eq. 4)
-    CK(launch_prep_dual(g, d_f, ws.R, ws.T, st), "prep");
-    CK(launch_copy(d_f, ws.u, (size_t)g->nx * g->ny * g->N, st), "copy");
+    LK(TNLM_KCLASS_PREP, launch_prep_dual(g, d_f, ws.R, ws.T, st), "prep");
+    LK(TNLM_KCLASS_PREP, launch_copy(d_f, ws.u, (size_t)g->nx * g->ny * g->N, st), "copy");
     ProjOut o{};
     o.mode = 1; o.r = ws.r; o.z = ws.z; o.y = d_y; o.sw = ws.sw; o.part = part_s;
-    CK(launch_project(g, ws.R, ws.T, o, st), "project");
-    CK(launch_backproject(g, ws.z, ws.s, part_i, st), "backproject");
-    CK(launch_cgls_init_scalars(g, ws, st), "scalars");
+    LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, o, st), "project");
+    LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.s, part_i, st), "backproject");
+    LK(TNLM_KCLASS_CGLS, launch_cgls_init_scalars(g, ws, st), "scalars");
     if (p->data_step == TNLM_DATA_GRAD) {
-        CK(launch_grad_final(g, ws, p->beta, st), "gradient step");
+        LK(TNLM_KCLASS_CGLS, launch_grad_final(g, ws, p->beta, st), "gradient step");
     } else {
         for (int m = 0; m < p->m1; ++m) {
             const bool last = m == p->m1 - 1;
-            CK(launch_prep_dual(g, ws.s, ws.R, ws.T, st), "prep");
+            LK(TNLM_KCLASS_PREP, launch_prep_dual(g, ws.s, ws.R, ws.T, st), "prep");
             ProjOut ot{};
             ot.mode = 2; ot.q = ws.t; ot.sw = ws.sw; ot.part = part_s;
-            CK(launch_project(g, ws.R, ws.T, ot, st), "project");
-            CK(launch_cgls_a(g, ws, st), "cgls a");
-            CK(launch_cgls_update_ur(g, ws, !last, st), "cgls update");
+            LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, ot, st), "project");
+            LK(TNLM_KCLASS_CGLS, launch_cgls_a(g, ws, st), "cgls a");
+            LK(TNLM_KCLASS_CGLS, launch_cgls_update_ur(g, ws, !last, st), "cgls update");
             if (last) break;
-            CK(launch_backproject(g, ws.z, ws.gr, part_i, st), "backproject");
-            CK(launch_cgls_b(g, ws, st), "cgls b");
-            CK(launch_cgls_update_s(g, ws, st), "cgls s");
+            LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.gr, part_i, st), "backproject");
+            LK(TNLM_KCLASS_CGLS, launch_cgls_b(g, ws, st), "cgls b");
+            LK(TNLM_KCLASS_CGLS, launch_cgls_update_s(g, ws, st), "cgls s");
         }
     }
     // ---- TNLM step: weights from g = ws.u, Gauss-Jacobi, positivity
     if (p->m2 > 0) {
-        CK(launch_weights(g, ws, p->patch, p->window, ws.u, st), "weights");
+        LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, ws, p->patch, p->window, ws.u, st), "weights");
         float* bufs[2] = {ws.U0, ws.U1};
         for (int m = 0; m < p->m2; ++m) {
             const bool last = m == p->m2 - 1;
-            CK(launch_gj_sweep(g, ws, p->window, p->h, p->mu_hat, ws.u, bufs[m & 1],
+            LK(TNLM_KCLASS_GJ, launch_gj_sweep(g, ws, p->window, p->h, p->mu_hat, ws.u, bufs[m & 1],
                                last ? nullptr : bufs[(m + 1) & 1], last ? d_f : nullptr, p->clamp,
                                st),
                "gauss-jacobi");
         }
     } else {
-        CK(launch_finalize_nogj(g, ws, ws.u, d_f, p->clamp, st), "finalize");
+        LK(TNLM_KCLASS_GJ, launch_finalize_nogj(g, ws, ws.u, d_f, p->clamp, st), "finalize");
     }
-    CK(launch_iter_scalars(g, ws, gj_blocks(g), st), "monitors");
+    LK(TNLM_KCLASS_CGLS, launch_iter_scalars(g, ws, gj_blocks(g), st), "monitors");
     return TNLM_OK;
 }
 
@@ -307,15 +356,32 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
         const double ga = (b - 0.5 * (g->B - 1)) * dg_;
         hb[b] = make_float2((float)cos(ga), (float)sin(ga));
     }
+    // Ray (view, bin): direction u = -(cos(t+g), sin(t+g)); in pixel units about
+    // the isocentre its line is u_x Y - u_y X = c0 with c0 = sid sin(g) / pixel.
+    // A ray with |u_x| >= |u_y| marches over columns: at the left edge of column
+    // k it is at row coordinate alpha + kk k; otherwise over rows, at column
+    // coordinate alpha + kk k at the bottom edge of row k.
+    const double hx = 0.5 * g->nx, hy = 0.5 * g->ny, sidp = g->sid / g->pixel;
     for (size_t v = 0; v < NV; ++v) {
         const double t = d->view_angles_rad[v];
         hv[v] = make_float2((float)cos(t), (float)sin(t));
         for (int b = 0; b < g->B; ++b) {
-            const double phi = t + (b - 0.5 * (g->B - 1)) * dg_;
-            const double ax = fabs(cos(phi)), ay = fabs(sin(phi));
-            const double lo = fmax(fmin(ax, ay), 1e-30), hi = fmax(ax, ay);
-            hr[v * g->B + b] = make_float4((float)(0.5 * (ax + ay)), (float)(1.0 / lo),
-                                           (float)(1.0 / hi), 0.f);
+            const double ga = (b - 0.5 * (g->B - 1)) * dg_;
+            const double ux = -cos(t + ga), uy = -sin(t + ga);
+            const double c0 = sidp * sin(ga);
+            double kk, alpha, ik, L;
+            if (fabs(ux) >= fabs(uy)) {
+                kk = uy / ux;
+                alpha = c0 / ux - kk * hx + hy;
+                ik = uy != 0.0 ? fabs(ux / uy) : INFINITY;
+                L = g->pixel / fabs(ux);
+            } else {
+                kk = ux / uy;
+                alpha = -c0 / uy - kk * hy + hx;
+                ik = ux != 0.0 ? fabs(uy / ux) : INFINITY;
+                L = -g->pixel / fabs(uy);
+            }
+            hr[v * g->B + b] = make_float4((float)kk, (float)alpha, (float)ik, (float)L);
         }
     }
     void *pv = nullptr, *pb = nullptr, *pr = nullptr;
@@ -349,7 +415,46 @@ void tnlm_destroy_geometry(tnlm_geometry* g) {
     cudaFree(g->d_bin);
     cudaFree(g->d_ray);
     cudaFree(g->ws.base);
+    if (g->prof) {
+        Profiler* P = (Profiler*)g->prof;
+        for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+        delete P;
+    }
     delete g;
+}
+
+tnlm_status tnlm_profile_enable(tnlm_geometry* g, unsigned int class_mask) {
+    g_err[0] = 0;
+    if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    if (class_mask >> TNLM_KCLASS_COUNT) return fail(TNLM_ERR_INVALID_ARG, "unknown kernel class in mask");
+    g->prof_mask = class_mask;
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_profile_read(tnlm_geometry* g, double* ms, long long* launches, int reset) {
+    g_err[0] = 0;
+    if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    CK(cudaDeviceSynchronize(), "sync");
+    double t[TNLM_KCLASS_COUNT] = {0, 0, 0, 0, 0, 0};
+    Profiler* P = (Profiler*)g->prof;
+    if (P) {
+        for (size_t k = 0; k < P->used; ++k) {
+            float e = 0.f;
+            CK(cudaEventElapsedTime(&e, P->ev[2 * k], P->ev[2 * k + 1]), "event time");
+            t[P->cls[k]] += e;
+        }
+    }
+    for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) {
+        if (ms) ms[c] = t[c];
+        if (launches) launches[c] = g->launches[c];
+    }
+    if (reset) {
+        if (P) P->used = 0;
+        for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) g->launches[c] = 0;
+    }
+    return TNLM_OK;
 }
 
 tnlm_status tnlm_project(const tnlm_geometry* gc, const float* d_img, float* d_sino, void* stream) {
@@ -363,10 +468,10 @@ tnlm_status tnlm_project(const tnlm_geometry* gc, const float* d_img, float* d_s
     cudaStream_t st = (cudaStream_t)stream;
     tnlm_status s = ensure_ws(g, g->ws.base ? g->ws.rho : 0, g->ws.base ? g->ws.kcap : 1, st);
     if (s != TNLM_OK) return s;
-    CK(launch_prep_dual(g, d_img, g->ws.R, g->ws.T, st), "prep");
+    LK(TNLM_KCLASS_PREP, launch_prep_dual(g, d_img, g->ws.R, g->ws.T, st), "prep");
     ProjOut o{};
     o.mode = 0; o.q = d_sino;
-    CK(launch_project(g, g->ws.R, g->ws.T, o, st), "project");
+    LK(TNLM_KCLASS_PROJECT, launch_project(g, g->ws.R, g->ws.T, o, st), "project");
     return TNLM_OK;
 }
 
@@ -377,7 +482,8 @@ tnlm_status tnlm_backproject(const tnlm_geometry* g, const float* d_sino, float*
     if (!aligned16(d_img) || !aligned16(d_sino)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     DeviceGuard dg(g->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
-    CK(launch_backproject(g, d_sino, d_img, nullptr, (cudaStream_t)stream), "backproject");
+    cudaStream_t st = (cudaStream_t)stream;
+    LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, d_sino, d_img, nullptr, st), "backproject");
     return TNLM_OK;
 }
 
@@ -418,9 +524,9 @@ tnlm_status tnlm_weights(const tnlm_geometry* gc, const tnlm_params* p, const fl
     cudaStream_t st = (cudaStream_t)stream;
     s = ensure_ws(g, (p->window - 1) / 2, g->ws.base ? g->ws.kcap : 1, st);
     if (s != TNLM_OK) return s;
-    CK(launch_weights(g, g->ws, p->patch, p->window, d_g, st), "weights");
-    CK(launch_weights_norm(g, g->ws, p->window, p->h, st), "weights normalisers");
-    CK(launch_weights_export(g, g->ws, p->window, d_dist, d_norm, st), "weights export");
+    LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, g->ws, p->patch, p->window, d_g, st), "weights");
+    LK(TNLM_KCLASS_WEIGHTS, launch_weights_norm(g, g->ws, p->window, p->h, st), "weights normalisers");
+    LK(TNLM_KCLASS_WEIGHTS, launch_weights_export(g, g->ws, p->window, d_dist, d_norm, st), "weights export");
     return TNLM_OK;
 }
 
@@ -442,7 +548,7 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* gc, const tnlm_params* p, cons
     Workspace& ws = g->ws;
     const size_t nsg = (size_t)g->N * g->V * g->B;
     CK(cudaMemsetAsync(ws.st.iter, 0, sizeof(int), st), "reset");
-    CK(launch_sqrt(d_winv, ws.sw, nsg, ws.st.err, st), "sqrt");
+    LK(TNLM_KCLASS_PREP, launch_sqrt(d_winv, ws.sw, nsg, ws.st.err, st), "sqrt");
     const bool sync = rep != nullptr || p->tol > 0.0;
     int done = 0;
     for (int k = 0; k < p->k_outer; ++k) {

@@ -26,7 +26,6 @@ namespace tnlm {
 constexpr int kMaxPatch = 15;
 constexpr int kMaxWindow = 31;
 constexpr int kProjThreads = 256;     // rays per projector block (one view)
-constexpr int kBpTile = 16;           // gather backprojector: 16 x 16 pixels per block
 constexpr int kWTileX = 32, kWTileY = 16;  // weight kernel output tile
 constexpr int kGjTileX = 32, kGjTileY = 8; // Gauss-Jacobi tile
 
@@ -81,8 +80,12 @@ struct tnlm_geometry {
     double pixel, bin_mm, sid, sdd;
     float2* d_view = nullptr;   // [N*V] (cos t, sin t)
     float2* d_bin = nullptr;    // [B] (cos g, sin g)
-    float4* d_ray = nullptr;    // [N*V*B] (ab2, 1/min(|ux|,|uy|), 1/max(|ux|,|uy|), 0)
+    float4* d_ray = nullptr;    // [N*V*B] per-ray marching constants (kk, alpha, 1/|kk|, +-L)
     tnlm::Workspace ws;
+    // profiling: launch counters and event-bracketed timing (see api.cu)
+    unsigned prof_mask = 0;
+    long long launches[TNLM_KCLASS_COUNT] = {0, 0, 0, 0, 0, 0};
+    void* prof = nullptr;
 };
 
 namespace tnlm {

@@ -13,15 +13,23 @@
 // which makes both classes' loads consecutive across the warp.  All lanes
 // of a warp walk the union of their column ranges in lock step.
 //
-// K2 (k_backproject): one thread per pixel, a gather over views -- no
-// atomics, so results are bitwise reproducible.  For a view, the bins whose
-// rays can touch the pixel lie within +-(1/sqrt 2)/dist of the pixel
-// centre's fan angle; for each, the exact chord of the line through the
-// square follows from the line's signed distance e to the pixel centre:
-// with a = |u_x|, b = |u_y|, chord = clamp(((a+b)/2 - |e|) / min(a,b), 0, 1) /
-// max(a,b) (a trapezoid in e whose area is the pixel area).  This is the
-// same matrix entry K1 accumulates, so K2 is the transpose of K1 up to FP32
-// rounding.
+// K2 (k_backproject): the transpose as an atomic-free gather.  A block owns
+// a 32 x 32 pixel tile of one phase; its 8 warps take every 8th view.  For a
+// view, the rays that can touch the tile form one bin range (from the fan
+// angles of the tile corners).  All 32 lanes of a warp handle the same ray at
+// once: for a column-marching ray lane c is tile column c and, with the very
+// same floating-point steps as K1, finds the ray's rows lo, lo+1 in that
+// column and adds frac * L * z and (1 - frac) * L * z to the warp's private
+// accumulator tile; a row-marching ray is handled the same way with lane c as
+// tile row c.  The private tiles are summed in a fixed order at the end, so
+// the result is bitwise reproducible, and every matrix entry is formed by the
+// same FP32 operations on the same per-ray constants as in K1.
+//
+// Per-ray constants (built in FP64 on the host at geometry creation):
+//   float4 (kk, alpha, ik, L): the position across the marching lines at the
+//   start of line k is alpha + kk*k (pixel units), ik = 1/|kk|, and L > 0 is
+//   the length per line (pixel / |u_x|) of a column-marching ray; L < 0 marks
+//   a row-marching ray (length -L per row).
 #include "internal.cuh"
 
 #include <math.h>
@@ -72,37 +80,50 @@ cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R,
 struct ProjArgs {
     const float* R;
     const float* T;
-    const float2* view;
-    const float2* bin;
+    const float4* ray;
     int nx, ny, V, B, nchunk;
-    float sidp;      // sid / pixel
-    float pixel;
     ProjOut o;
 };
+
+// Lower of the two across-line positions of a ray inside line k, its lower
+// line index clamped into the zero pads [-1, nacross], and the fraction of
+// the line's width where the ray lies in that line.  K1 and K2 both use this,
+// so they form every matrix entry with identical FP32 operations.
+struct Cut {
+    float frac;
+    int j;
+};
+__device__ __forceinline__ Cut line_cut(float kk, float am, float ik, float kf, float nacross_f) {
+    const float mn = fmaf(kk, kf, am);
+    const float fl = fminf(fmaxf(floorf(mn), -1.f), nacross_f);
+    Cut c;
+    c.frac = fminf(1.f, fmaf(fl - mn, ik, ik));
+    // exact float -> int of a small integer-valued float
+    c.j = __float_as_int(fl + 12582912.f) - 0x4B400000;
+    return c;
+}
 
 // March one ray over 'lines' (columns of T or rows of R) lo..hi.  base points
 // at the first interior element of line 0 of the phase; 'pitch' is the line
 // stride; 'nacross' the interior length of a line.  The position across the
-// line at the start of line k is alpha + kk*k (pixel units).
+// line at the start of line k is alpha + kk*k (pixel units); am = alpha +
+// min(kk, 0) is the lower end of the ray's span inside line 0.
 __device__ __forceinline__ float march(const float* __restrict__ base, int pitch, int nacross,
-                                       float kk, float alpha, float ik, int lo, int hi, bool on) {
+                                       float kk, float am, float ik, int lo, int hi, bool on) {
     float acc = 0.f;
-#pragma unroll 2
+    float kf = (float)lo;
+    int koff = lo * pitch;
+    const float na = (float)nacross;
+#pragma unroll 4
     for (int k = lo; k <= hi; ++k) {
-        const float c0 = fmaf(kk, (float)k, alpha);
-        const float mn = fminf(c0, c0 + kk);
-        // clamp the lower line index into the zero pads [-1, nacross]; the
-        // fraction is taken w.r.t. the clamped index, so a ray entirely
-        // below (above) the image puts all (no) weight on pad line -1
-        // (lines nacross, nacross+1), i.e. contributes zero.
-        const float fl = fminf(fmaxf(floorf(mn), -1.f), (float)nacross);
-        const float frac = fminf(1.f, (fl + 1.f - mn) * ik);
-        const int j = (int)fl;
+        const Cut c = line_cut(kk, am, ik, kf, na);
         if (on) {
-            const float* p = base + (size_t)k * pitch + j;
+            const float* p = base + (koff + c.j);
             const float v0 = __ldg(p), v1 = __ldg(p + 1);
-            acc = fmaf(frac, v0 - v1, acc + v1);
+            acc = fmaf(c.frac, v0 - v1, acc + v1);
         }
+        kf += 1.f;
+        koff += pitch;
     }
     return acc;
 }
@@ -132,50 +153,28 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
     const int phase = gv / a.V;
     const int b = chunk * kProjThreads + threadIdx.x;
     const bool valid = b < a.B;
-    const float2 vt = a.view[gv];
-    const float2 bt = a.bin[valid ? b : 0];
-    // ray direction u = -(cos(t+g), sin(t+g)); line: u_x*Y - u_y*X = c0 in
-    // pixel units about the isocentre, c0 = sid*sin(g)/pixel.
-    const float ux = -(vt.x * bt.x - vt.y * bt.y);
-    const float uy = -(vt.y * bt.x + vt.x * bt.y);
-    const float c0 = a.sidp * bt.y;
-    const bool colm = fabsf(ux) >= fabsf(uy);
-    const float hx = 0.5f * a.nx, hy = 0.5f * a.ny;
+    const float4 rp = a.ray[(size_t)gv * a.B + (valid ? b : 0)];
+    const bool colm = rp.w > 0.f;
 
     float q = 0.f;
     const unsigned full = 0xffffffffu;
-    // --- column-marching class (reads T) ---
-    {
-        const bool in = valid && colm;
-        const float kk = uy / ux;
-        const float alpha = c0 / ux - kk * hx + hy;   // row coordinate at column 0
-        const float ik = fabsf(ux / uy);
+#pragma unroll
+    for (int cls = 0; cls < 2; ++cls) {
+        // cls 0: column-marching rays read T; cls 1: row-marching rays read R
+        const bool in = valid && (cls == 0 ? colm : !colm);
+        const int nlines = cls == 0 ? a.nx : a.ny;
+        const int nacross = cls == 0 ? a.ny : a.nx;
         int lo = 1, hi = 0;
-        if (in) line_range(kk, alpha, a.nx, a.ny, &lo, &hi);
-        const unsigned m = __ballot_sync(full, in && hi >= lo);
-        if (m) {
-            const int wl = __reduce_min_sync(full, (in && hi >= lo) ? lo : 0x7fffffff);
-            const int wh = __reduce_max_sync(full, (in && hi >= lo) ? hi : -1);
-            const float* base = a.T + (size_t)phase * a.nx * (a.ny + 4) + 2;
-            const float acc = march(base, a.ny + 4, a.ny, kk, alpha, ik, wl, wh, in);
-            if (in) q = acc * (a.pixel / fabsf(ux));
-        }
-    }
-    // --- row-marching class (reads R) ---
-    {
-        const bool in = valid && !colm;
-        const float kk = ux / uy;
-        const float alpha = -c0 / uy - kk * hy + hx;  // column coordinate at row 0
-        const float ik = fabsf(uy / ux);
-        int lo = 1, hi = 0;
-        if (in) line_range(kk, alpha, a.ny, a.nx, &lo, &hi);
-        const unsigned m = __ballot_sync(full, in && hi >= lo);
-        if (m) {
-            const int wl = __reduce_min_sync(full, (in && hi >= lo) ? lo : 0x7fffffff);
-            const int wh = __reduce_max_sync(full, (in && hi >= lo) ? hi : -1);
-            const float* base = a.R + (size_t)phase * a.ny * (a.nx + 4) + 2;
-            const float acc = march(base, a.nx + 4, a.nx, kk, alpha, ik, wl, wh, in);
-            if (in) q = acc * (a.pixel / fabsf(uy));
+        if (in) line_range(rp.x, rp.y, nlines, nacross, &lo, &hi);
+        const bool any = in && hi >= lo;
+        if (__ballot_sync(full, any)) {
+            const int wl = __reduce_min_sync(full, any ? lo : 0x7fffffff);
+            const int wh = __reduce_max_sync(full, any ? hi : -1);
+            const float* base = cls == 0 ? a.T + (size_t)phase * a.nx * (a.ny + 4) + 2
+                                         : a.R + (size_t)phase * a.ny * (a.nx + 4) + 2;
+            const float acc = march(base, nacross + 4, nacross, rp.x, rp.y + fminf(rp.x, 0.f), rp.z,
+                                    wl, wh, in);
+            if (in) q = acc * fabsf(rp.w);
         }
     }
 
@@ -210,10 +209,8 @@ int proj_chunks(const tnlm_geometry* g) { return (g->B + kProjThreads - 1) / kPr
 cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
                            const ProjOut& o, cudaStream_t st) {
     ProjArgs a;
-    a.R = R; a.T = T; a.view = g->d_view; a.bin = g->d_bin;
+    a.R = R; a.T = T; a.ray = g->d_ray;
     a.nx = g->nx; a.ny = g->ny; a.V = g->V; a.B = g->B; a.nchunk = proj_chunks(g);
-    a.sidp = (float)(g->sid / g->pixel);
-    a.pixel = (float)g->pixel;
     a.o = o;
     dim3 grid(a.nchunk * g->N * g->V);
     switch (o.mode) {
@@ -227,87 +224,161 @@ cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* 
 // ---------------------------------------------------------------------------
 // K2
 // ---------------------------------------------------------------------------
+constexpr int kBpT = 32;        // tile side
+constexpr int kBpWarps = 8;
+
 struct BpArgs {
     const float* sino;
     float* img;
     double* part;          // nullable: per-block partial sums of img^2
     const float2* view;
-    const float2* bin;
     const float4* ray;
     int nx, ny, V, B;
-    float sidp, pixel, inv_dg, half_b;
+    float sidp, inv_dg, half_b;
 };
 
-template <bool PART>
-__global__ void __launch_bounds__(kBpTile * kBpTile) k_backproject(BpArgs a) {
-    extern __shared__ float2 s_bin[];          // [B] (cos g, sin g)
-    const int tid = threadIdx.x;
-    for (int k = tid; k < a.B; k += blockDim.x) s_bin[k] = a.bin[k];
-    __syncthreads();
-    // 8 warps, each an 8 x 4 pixel sub-tile (compact footprint on the detector)
-    const int w = tid >> 5, l = tid & 31;
-    const int lx = (l & 7) + 8 * (w & 1);
-    const int ly = (l >> 3) + 4 * (w >> 1);
-    const int ix = blockIdx.x * kBpTile + lx, iy = blockIdx.y * kBpTile + ly;
-    const int phase = blockIdx.z;
-    const bool inside = ix < a.nx && iy < a.ny;
-    const float cx = (float)ix - 0.5f * (a.nx - 1);
-    const float cy = (float)iy - 0.5f * (a.ny - 1);
-    const float hwk = 0.70711f * 1.0001f * a.inv_dg;
+size_t bp_smem_bytes() {
+    return sizeof(float) * (2 * kBpWarps * kBpT * kBpT + kBpT * (kBpT + 1)) +
+           sizeof(float4) * kBpWarps * 32;
+}
 
-    float acc = 0.f;
-    if (inside) {
-        const float2* vtab = a.view + (size_t)phase * a.V;
-        for (int v = 0; v < a.V; ++v) {
-            const float2 vt = vtab[v];
-            // X = cross(c_dir, c - S), Y = dot(c_dir, c - S), c_dir = -(cos t, sin t)
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Add frac * Lz to line j and (1 - frac) * Lz to line j + 1 of a private
+// accumulator column (tile-local index j relative to j0, n lines).
+__device__ __forceinline__ void deposit(float* acc, float kk, float am, float ik, float Lz,
+                                        int k, int j0, int n, int nacross) {
+    const Cut c = line_cut(kk, am, ik, (float)k, (float)nacross);
+    const int r0 = c.j - j0;
+    if (r0 >= 0 && r0 < n) acc[r0 * 32] += c.frac * Lz;
+    if (r0 + 1 >= 0 && r0 + 1 < n) acc[(r0 + 1) * 32] += (1.f - c.frac) * Lz;
+}
+
+template <bool PART>
+__global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
+    extern __shared__ float sm[];
+    float* accC = sm;                                   // [warp][row][col]
+    float* accR = accC + kBpWarps * kBpT * kBpT;        // [warp][col][row]
+    float* tsum = accR + kBpWarps * kBpT * kBpT;        // [row][col + 1]
+    float4* stg = (float4*)(tsum + kBpT * (kBpT + 1));  // [warp][32]
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const int X0 = blockIdx.x * kBpT, Y0 = blockIdx.y * kBpT, phase = blockIdx.z;
+    const int ncols = min(kBpT, a.nx - X0), nrows = min(kBpT, a.ny - Y0);
+    for (int k = tid; k < 2 * kBpWarps * kBpT * kBpT; k += blockDim.x) sm[k] = 0.f;
+    __syncthreads();
+    float* myC = accC + w * kBpT * kBpT + lane;
+    float* myR = accR + w * kBpT * kBpT + lane;
+    float4* myS = stg + w * 32;
+    // tile corners (pixel units about the isocentre), clipped to the image
+    const float xa = X0 - 0.5f * a.nx, xb = X0 + ncols - 0.5f * a.nx;
+    const float ya = Y0 - 0.5f * a.ny, yb = Y0 + nrows - 0.5f * a.ny;
+    const unsigned full = 0xffffffffu;
+
+    for (int v = w; v < a.V; v += kBpWarps) {
+        const size_t gv = (size_t)phase * a.V + v;
+        const float2 vt = a.view[gv];
+        float bmin = 3e30f, bmax = -3e30f;
+        if (lane < 4) {
+            const float cx = (lane & 1) ? xb : xa, cy = (lane & 2) ? yb : ya;
             const float X = vt.y * cx - vt.x * cy;
             const float Y = a.sidp - (vt.x * cx + vt.y * cy);
-            const float gc = atanf(X / Y);
-            const float bc = fmaf(gc, a.inv_dg, a.half_b);
-            const float hw = hwk / Y + 1e-3f;
-            const int b0 = max(0, (int)ceilf(bc - hw));
-            const int b1 = min(a.B - 1, (int)floorf(bc + hw));
-            const size_t rbase = ((size_t)phase * a.V + v) * a.B;
-            for (int b = b0; b <= b1; ++b) {
-                const float2 gb = s_bin[b];
-                const float4 rp = __ldg(a.ray + rbase + b);
-                const float e = gb.x * X - gb.y * Y;           // signed distance (pixels)
-                const float frac = __saturatef((rp.x - fabsf(e)) * rp.y);
-                acc = fmaf(frac * rp.z, __ldg(a.sino + rbase + b), acc);
+            bmin = bmax = fmaf(atanf(X / Y), a.inv_dg, a.half_b);
+        }
+        bmin = warp_min(bmin);
+        bmax = warp_max(bmax);
+        const int b_lo = max(0, (int)floorf(bmin) - 1);
+        const int b_hi = min(a.B - 1, (int)ceilf(bmax) + 1);
+        const float4* rays = a.ray + gv * a.B;
+        const float* z = a.sino + gv * a.B;
+        for (int b0 = b_lo; b0 <= b_hi; b0 += 32) {
+            const int nb = min(32, b_hi - b0 + 1);
+            float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lane < nb) rp = __ldg(rays + b0 + lane);
+            // bit t: staged ray t marches over columns (L > 0)
+            const unsigned colmask = __ballot_sync(full, lane < nb && rp.w > 0.f);
+            const float Lz = lane < nb ? fabsf(rp.w) * __ldg(z + b0 + lane) : 0.f;
+            __syncwarp();
+            myS[lane] = make_float4(rp.x, rp.y + fminf(rp.x, 0.f), rp.z, Lz);
+            __syncwarp();
+            for (int t = 0; t < nb; ++t) {
+                const float4 r = myS[t];
+                if ((colmask >> t) & 1u) {
+                    if (lane < ncols) deposit(myC, r.x, r.y, r.z, r.w, X0 + lane, Y0, nrows, a.ny);
+                } else {
+                    if (lane < nrows) deposit(myR, r.x, r.y, r.z, r.w, Y0 + lane, X0, ncols, a.nx);
+                }
             }
         }
-        acc *= a.pixel;
-        a.img[((size_t)phase * a.ny + iy) * a.nx + ix] = acc;
+    }
+    __syncthreads();
+    // fixed-order reduction of the private tiles
+    for (int k = tid; k < kBpT * kBpT; k += blockDim.x) {
+        const int r = k >> 5, c = k & 31;
+        float s = 0.f;
+#pragma unroll
+        for (int ww = 0; ww < kBpWarps; ++ww) s += accC[(ww * kBpT + r) * kBpT + c];
+        tsum[r * (kBpT + 1) + c] = s;
+    }
+    __syncthreads();
+    for (int k = tid; k < kBpT * kBpT; k += blockDim.x) {
+        const int c = k >> 5, r = k & 31;
+        float s = tsum[r * (kBpT + 1) + c];
+#pragma unroll
+        for (int ww = 0; ww < kBpWarps; ++ww) s += accR[(ww * kBpT + c) * kBpT + r];
+        tsum[r * (kBpT + 1) + c] = s;
+    }
+    __syncthreads();
+    float sq = 0.f;
+    for (int k = tid; k < kBpT * kBpT; k += blockDim.x) {
+        const int r = k >> 5, c = k & 31;
+        if (r < nrows && c < ncols) {
+            const float v = tsum[r * (kBpT + 1) + c];
+            a.img[((size_t)phase * a.ny + Y0 + r) * a.nx + X0 + c] = v;
+            sq = fmaf(v, v, sq);
+        }
     }
     if (PART) {
-        __shared__ double sh[kBpTile * kBpTile / 32];
-        const double tot = block_sum<kBpTile * kBpTile>(inside ? acc * acc : 0.f, sh, tid);
+        __shared__ double sh[kBpWarps];
+        const double tot = block_sum<kBpWarps * 32>(sq, sh, tid);
         if (tid == 0)
             a.part[(size_t)phase * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = tot;
     }
 }
 
 int bp_blocks_per_phase(const tnlm_geometry* g) {
-    return ((g->nx + kBpTile - 1) / kBpTile) * ((g->ny + kBpTile - 1) / kBpTile);
+    return ((g->nx + kBpT - 1) / kBpT) * ((g->ny + kBpT - 1) / kBpT);
 }
 
 cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float* img,
                                double* part, cudaStream_t st) {
     BpArgs a;
     a.sino = sino; a.img = img; a.part = part;
-    a.view = g->d_view; a.bin = g->d_bin; a.ray = g->d_ray;
+    a.view = g->d_view; a.ray = g->d_ray;
     a.nx = g->nx; a.ny = g->ny; a.V = g->V; a.B = g->B;
     a.sidp = (float)(g->sid / g->pixel);
-    a.pixel = (float)g->pixel;
     a.inv_dg = (float)(g->sdd / g->bin_mm);
     a.half_b = 0.5f * (float)(g->B - 1);
-    dim3 grid((g->nx + kBpTile - 1) / kBpTile, (g->ny + kBpTile - 1) / kBpTile, g->N);
-    const size_t smem = sizeof(float2) * g->B;
-    if (part)
-        k_backproject<true><<<grid, kBpTile * kBpTile, smem, st>>>(a);
-    else
-        k_backproject<false><<<grid, kBpTile * kBpTile, smem, st>>>(a);
+    dim3 grid((g->nx + kBpT - 1) / kBpT, (g->ny + kBpT - 1) / kBpT, g->N);
+    const size_t smem = bp_smem_bytes();
+    cudaError_t e;
+    if (part) {
+        e = cudaFuncSetAttribute(k_backproject<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_backproject<true><<<grid, kBpWarps * 32, smem, st>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_backproject<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_backproject<false><<<grid, kBpWarps * 32, smem, st>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -236,7 +236,9 @@ __global__ void __launch_bounds__(kGjTileX * kGjTileY) k_gj(GjArgs a) {
                 zb += eb;
             }
         }
-        if (!(zf >= 1.f) || !(zb >= 1.f)) atomicOr(a.err, 8);
+        // the row minimum contributes 2^(rounding error of m*k2) ~ 1, so a
+        // normaliser below 1/2 (or NaN) means a non-finite distance or image
+        if (!(zf >= 0.5f) || !(zb >= 0.5f)) atomicOr(a.err, 8);
     }
     if (MODE == 2) {
         if (in) {
@@ -266,8 +268,153 @@ __global__ void __launch_bounds__(kGjTileX * kGjTileY) k_gj(GjArgs a) {
     }
 }
 
-int gj_blocks(const tnlm_geometry* g) {
+// Vectorised sweep for W in {3, 5, ..., 15}: a thread owns 4 consecutive
+// pixels of one row.  Per window row it loads the neighbour-phase values it
+// needs as aligned float4 windows into registers; per shift it loads the
+// forward distances as one float4 and the backward ones from an aligned
+// 8-float window at a compile-time offset.  Requires the padded layout with
+// ox >= align4(rho) + 4 and px a multiple of 4 (see the workspace layout).
+constexpr int kGjvPx = 4;              // pixels per thread
+constexpr int kGjvTx = 16, kGjvTy = 16;  // threads per block in x (64 px) and y
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(kGjvTx * kGjvTy) k_gj_vec(GjArgs a) {
+    constexpr int RHO = (W - 1) / 2;
+    constexpr int UOFF = 4 * ((RHO + 3) / 4);
+    constexpr int UW = 4 + 2 * UOFF;
+    const int N = a.N, nx = a.nx, ny = a.ny;
+    const int tile = blockIdx.x / N, i = blockIdx.x % N;
+    const int tilesx = (nx + kGjvTx * kGjvPx - 1) / (kGjvTx * kGjvPx);
+    const int tid = threadIdx.x;
+    const int x0 = (tile % tilesx) * (kGjvTx * kGjvPx) + kGjvPx * (tid % kGjvTx);
+    const int y = (tile / tilesx) * kGjvTy + tid / kGjvTx;
+    const bool rowin = x0 < nx && y < ny;
+    const size_t npx = (size_t)nx * ny;
+    const int ip = (i + N - 1) % N, inx = (i + 1) % N;
+    const int px = a.pp.px;
+    const int plane = (int)a.pp.plane;
+    float af[4] = {0.f, 0.f, 0.f, 0.f}, zf[4] = {0.f, 0.f, 0.f, 0.f};
+    float ab[4] = {0.f, 0.f, 0.f, 0.f}, zb[4] = {0.f, 0.f, 0.f, 0.f};
+    const float k2 = a.k2;
+    if (rowin) {
+        float mfk[4], mbk[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const bool in = x0 + p < nx;
+            const size_t pix = (size_t)y * nx + x0 + p;
+            mfk[p] = in ? a.mins[i * npx + pix] * k2 : 0.f;
+            mbk[p] = in ? a.mins[(N + i) * npx + pix] * k2 : 0.f;
+        }
+        const int c0 = x0 + a.pp.ox;                    // padded column of pixel x0
+        const float* Dn = a.D + (size_t)i * (W * W) * a.pp.plane + (size_t)(y + a.pp.oy) * px + c0;
+        const float* Dp = a.D + (size_t)ip * (W * W) * a.pp.plane + (size_t)(y + a.pp.oy) * px + c0;
+        const float* Un = a.uin + (size_t)inx * a.pp.plane + (size_t)(y + a.pp.oy) * px + c0 - UOFF;
+        const float* Up = a.uin + (size_t)ip * a.pp.plane + (size_t)(y + a.pp.oy) * px + c0 - UOFF;
+        for (int sy = 0; sy < W; ++sy) {
+            const int dy = sy - RHO;
+            float un[UW], up[UW];
+#pragma unroll
+            for (int q = 0; q < UW / 4; ++q) {
+                const float4 vn = __ldg((const float4*)(Un + dy * px) + q);
+                const float4 vp = __ldg((const float4*)(Up - dy * px) + q);
+                un[4 * q] = vn.x; un[4 * q + 1] = vn.y; un[4 * q + 2] = vn.z; un[4 * q + 3] = vn.w;
+                up[4 * q] = vp.x; up[4 * q + 1] = vp.y; up[4 * q + 2] = vp.z; up[4 * q + 3] = vp.w;
+            }
+#pragma unroll
+            for (int sx = 0; sx < W; ++sx) {
+                const int dx = sx - RHO;
+                const int k = sy * W + sx;
+                const float4 f4 = __ldg((const float4*)(Dn + k * plane));
+                const float df[4] = {f4.x, f4.y, f4.z, f4.w};
+                // backward distances at columns x0 - dx .. x0 - dx + 3, row y - dy
+                const int off = -dx;
+                const int base = off >= 0 ? (off / 4) * 4 : -(((-off) + 3) / 4) * 4;
+                const int sh = off - base;
+                const float* pb = Dp + k * plane - dy * px + base;
+                const float4 b0 = __ldg((const float4*)pb);
+                float w8[8] = {b0.x, b0.y, b0.z, b0.w, 0.f, 0.f, 0.f, 0.f};
+                if (sh != 0) {
+                    const float4 b1 = __ldg((const float4*)pb + 1);
+                    w8[4] = b1.x; w8[5] = b1.y; w8[6] = b1.z; w8[7] = b1.w;
+                }
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float ef = ex2_approx(fmaf(-df[p], k2, mfk[p]));
+                    const float eb = ex2_approx(fmaf(-w8[sh + p], k2, mbk[p]));
+                    if (MODE != 2) {
+                        af[p] = fmaf(ef, un[UOFF + p + dx], af[p]);
+                        ab[p] = fmaf(eb, up[UOFF + p - dx], ab[p]);
+                    }
+                    zf[p] += ef;
+                    zb[p] += eb;
+                }
+            }
+        }
+    }
+    float dsq = 0.f, nsq = 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const int x = x0 + p;
+        if (!rowin || x >= nx) continue;
+        bad |= !(zf[p] >= 0.5f) || !(zb[p] >= 0.5f);
+        const size_t pix = (size_t)y * nx + x;
+        if (MODE == 2) {
+            a.zn[i * npx + pix] = zf[p];
+            a.zn[(N + i) * npx + pix] = zb[p];
+            continue;
+        }
+        const float unew = fmaf(a.g[i * npx + pix], a.c1, a.c2 * (af[p] / zf[p] + ab[p] / zb[p]));
+        if (MODE == 0) {
+            a.uout[i * a.pp.plane + (size_t)(y + a.pp.oy) * px + x + a.pp.ox] = unew;
+        } else {
+            const float fnew = a.clamp ? fmaxf(unew, 0.f) : unew;
+            const float fold = a.fout[i * npx + pix];
+            a.fout[i * npx + pix] = fnew;
+            dsq = fmaf(fnew - fold, fnew - fold, dsq);
+            nsq = fmaf(fnew, fnew, nsq);
+        }
+    }
+    if (bad) atomicOr(a.err, 8);
+    if (MODE == 1) {
+        __shared__ double sh[kGjvTx * kGjvTy / 32];
+        const double d2 = block_sum<kGjvTx * kGjvTy>(dsq, sh, tid);
+        const double n2 = block_sum<kGjvTx * kGjvTy>(nsq, sh, tid);
+        if (tid == 0) {
+            a.part[2 * (size_t)blockIdx.x] = d2;
+            a.part[2 * (size_t)blockIdx.x + 1] = n2;
+        }
+    }
+}
+
+static int gjv_blocks(const tnlm_geometry* g) {
+    const int tx = (g->nx + kGjvTx * kGjvPx - 1) / (kGjvTx * kGjvPx);
+    const int ty = (g->ny + kGjvTy - 1) / kGjvTy;
+    return tx * ty * g->N;
+}
+
+template <int MODE>
+static bool launch_gj_vec(const GjArgs& a, int window, int nb, cudaStream_t st) {
+    const int th = kGjvTx * kGjvTy;
+    switch (window) {
+        case 3: k_gj_vec<3, MODE><<<nb, th, 0, st>>>(a); return true;
+        case 5: k_gj_vec<5, MODE><<<nb, th, 0, st>>>(a); return true;
+        case 7: k_gj_vec<7, MODE><<<nb, th, 0, st>>>(a); return true;
+        case 9: k_gj_vec<9, MODE><<<nb, th, 0, st>>>(a); return true;
+        case 11: k_gj_vec<11, MODE><<<nb, th, 0, st>>>(a); return true;
+        case 13: k_gj_vec<13, MODE><<<nb, th, 0, st>>>(a); return true;
+        case 15: k_gj_vec<15, MODE><<<nb, th, 0, st>>>(a); return true;
+        default: return false;
+    }
+}
+
+// Number of relative-change partial slots used by the sweep / finalisation.
+static int gjs_blocks(const tnlm_geometry* g) {
     return ((g->nx + kGjTileX - 1) / kGjTileX) * ((g->ny + kGjTileY - 1) / kGjTileY) * g->N;
+}
+int gj_blocks(const tnlm_geometry* g) {
+    const int a = gjs_blocks(g), b = gjv_blocks(g);
+    return a > b ? a : b;
 }
 
 static GjArgs gj_args(const tnlm_geometry* g, const Workspace& ws, int window, double h,
@@ -287,11 +434,18 @@ cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int win
                             float* fout, int clamp, cudaStream_t st) {
     GjArgs a = gj_args(g, ws, window, h, mu_hat);
     a.g = gimg; a.uin = uin; a.uout = uout; a.fout = fout; a.clamp = clamp;
-    const int nb = gj_blocks(g);
+    // the partial slots not written by this launch must read as zero
+    const int nv = gjv_blocks(g), ns = gjs_blocks(g);
+    if (ws.pp.ox >= ((a.rho + 3) / 4) * 4 + 4 && (ws.pp.px % 4) == 0 &&
+        (fout ? launch_gj_vec<1>(a, window, nv, st) : launch_gj_vec<0>(a, window, nv, st))) {
+        if (fout && ns > nv) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nv, 0, 16 * (size_t)(ns - nv), st);
+        return cudaGetLastError();
+    }
     if (fout)
-        k_gj<1><<<nb, kGjTileX * kGjTileY, 0, st>>>(a);
+        k_gj<1><<<ns, kGjTileX * kGjTileY, 0, st>>>(a);
     else
-        k_gj<0><<<nb, kGjTileX * kGjTileY, 0, st>>>(a);
+        k_gj<0><<<ns, kGjTileX * kGjTileY, 0, st>>>(a);
+    if (fout && nv > ns) return cudaMemsetAsync(ws.part2 + 2 * (size_t)ns, 0, 16 * (size_t)(nv - ns), st);
     return cudaGetLastError();
 }
 
@@ -299,7 +453,7 @@ cudaError_t launch_weights_norm(const tnlm_geometry* g, const Workspace& ws, int
                                 cudaStream_t st) {
     GjArgs a = gj_args(g, ws, window, h, 0.0);
     a.uin = ws.U0;
-    k_gj<2><<<gj_blocks(g), kGjTileX * kGjTileY, 0, st>>>(a);
+    k_gj<2><<<gjs_blocks(g), kGjTileX * kGjTileY, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -332,7 +486,9 @@ __global__ void __launch_bounds__(256) k_finalize_nogj(const float* __restrict__
 
 cudaError_t launch_finalize_nogj(const tnlm_geometry* g, const Workspace& ws, const float* gimg,
                                  float* fout, int clamp, cudaStream_t st) {
-    k_finalize_nogj<<<gj_blocks(g), 256, 0, st>>>(gimg, fout, ws.part2, g->nx, g->ny, g->N, clamp);
+    const int ns = gjs_blocks(g), nv = gjv_blocks(g);
+    k_finalize_nogj<<<ns, 256, 0, st>>>(gimg, fout, ws.part2, g->nx, g->ny, g->N, clamp);
+    if (nv > ns) return cudaMemsetAsync(ws.part2 + 2 * (size_t)ns, 0, 16 * (size_t)(nv - ns), st);
     return cudaGetLastError();
 }
 
