@@ -191,10 +191,11 @@ def run_gpu(args):
         tn.tnlm_profile_enable(s["geo"], tn.KCLASSES)
     for _ in range(max(args.warmup, 3)):
         step()
-    prof = {}
+    prof, prof_n = {}, {}
     for s in slices:
         for k, v in tn.tnlm_profile_read(s["geo"]).items():
             prof[k] = prof.get(k, 0.0) + v["ms"]
+            prof_n[k] = prof_n.get(k, 0) + v["launches"]
     dominant = max(prof, key=prof.get)
     for s in slices:
         tn.tnlm_profile_enable(s["geo"], (dominant,))
@@ -279,6 +280,20 @@ def run_gpu(args):
             roof = {"bound": bound, "kernel": dominant, "achieved": round(achieved, 3),
                     "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
                     "traffic": None, "peak_source": src, "launch_ms": round(per_launch_ms, 4)}
+        # every kernel class, from the warm-up pass in which all classes were timed
+        by_kernel = {}
+        for cls in ("project", "backproject", "weights", "gj"):
+            amt_c = np.mean([roofline_units(c, cls)[0] for c in cases])
+            _, unit_c, bound_c = roofline_units(cases[0], cls)
+            ms_c = prof.get(cls, 0.0) / max(prof_n.get(cls, 0), 1)
+            if ms_c <= 0:
+                continue
+            if unit_c == "GB/s":
+                ach, pk = amt_c / (ms_c / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0)
+            else:
+                ach, pk = amt_c / (ms_c / 1e3) / 1e12, fp32_peak_tflops()
+            by_kernel[cls] = {"bound": bound_c, "achieved": round(ach, 3), "peak": round(pk, 1),
+                              "unit": unit_c, "frac": round(ach / pk, 4), "launch_ms": round(ms_c, 4)}
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
@@ -292,6 +307,7 @@ def run_gpu(args):
             "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
+            "roofline_by_kernel": by_kernel,
             "kernel_ms_share": {k: round(v / max(sum(prof.values()), 1e-9), 4) for k, v in prof.items()},
         }
         if not args.no_cpu_baseline:

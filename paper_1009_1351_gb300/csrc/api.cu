@@ -139,7 +139,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Byte layout of the workspace for window radius rho and history capacity kcap.
 struct WsLayout {
-    size_t off_u, off_s, off_gr, off_R, off_T, off_r, off_z, off_t, off_sw, off_D, off_U0, off_U1,
+    size_t off_u, off_s, off_gr, off_R, off_T, off_r, off_z, off_t, off_sw, off_bps, off_D, off_U0, off_U1,
         off_mins, off_zn, off_part, off_part2, off_state, total;
     size_t part_len, part2_len;
     PadPlane pp;
@@ -169,6 +169,7 @@ WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
     L.off_z = take(4 * nsg * N);
     L.off_t = take(4 * nsg * N);
     L.off_sw = take(4 * nsg * N);
+    L.off_bps = take(4 * bp_scratch_floats(g));
     L.off_D = take(4 * L.pp.plane * W2 * N);
     L.off_U0 = take(4 * L.pp.plane * N);
     L.off_U1 = take(4 * L.pp.plane * N);
@@ -216,6 +217,7 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     ws.z = (float*)(b + L.off_z);
     ws.t = (float*)(b + L.off_t);
     ws.sw = (float*)(b + L.off_sw);
+    ws.bps = (float*)(b + L.off_bps);
     ws.pp = L.pp;
     ws.D = (float*)(b + L.off_D);
     ws.U0 = (float*)(b + L.off_U0);
@@ -261,7 +263,7 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     ProjOut o{};
     o.mode = 1; o.r = ws.r; o.z = ws.z; o.y = d_y; o.sw = ws.sw; o.part = part_s;
     LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, o, st), "project");
-    LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.s, part_i, st), "backproject");
+    LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.s, part_i, ws.bps, st), "backproject");
     LK(TNLM_KCLASS_CGLS, launch_cgls_init_scalars(g, ws, st), "scalars");
     if (p->data_step == TNLM_DATA_GRAD) {
         LK(TNLM_KCLASS_CGLS, launch_grad_final(g, ws, p->beta, st), "gradient step");
@@ -275,7 +277,7 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
             LK(TNLM_KCLASS_CGLS, launch_cgls_a(g, ws, st), "cgls a");
             LK(TNLM_KCLASS_CGLS, launch_cgls_update_ur(g, ws, !last, st), "cgls update");
             if (last) break;
-            LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.gr, part_i, st), "backproject");
+            LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.gr, part_i, ws.bps, st), "backproject");
             LK(TNLM_KCLASS_CGLS, launch_cgls_b(g, ws, st), "cgls b");
             LK(TNLM_KCLASS_CGLS, launch_cgls_update_s(g, ws, st), "cgls s");
         }
@@ -295,6 +297,67 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
         LK(TNLM_KCLASS_GJ, launch_finalize_nogj(g, ws, ws.u, d_f, p->clamp, st), "finalize");
     }
     LK(TNLM_KCLASS_CGLS, launch_iter_scalars(g, ws, gj_blocks(g), st), "monitors");
+    return TNLM_OK;
+}
+
+// One outer iteration captured as a CUDA graph on a handle-owned stream and
+// replayed on the caller's stream.  The key is everything the captured
+// launches depend on: the parameters that shape them, the caller's y and f
+// pointers and the workspace allocation.
+struct GraphState {
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    tnlm_params p{};
+    const float* y = nullptr;
+    float* f = nullptr;
+    void* ws = nullptr;
+    long long launches[TNLM_KCLASS_COUNT] = {0, 0, 0, 0, 0, 0};  // kernels per replay
+};
+
+bool same_shape(const tnlm_params& a, const tnlm_params& b) {
+    return a.mu_hat == b.mu_hat && a.h == b.h && a.beta == b.beta && a.patch == b.patch &&
+           a.window == b.window && a.m1 == b.m1 && a.m2 == b.m2 && a.data_step == b.data_step &&
+           a.clamp == b.clamp;
+}
+
+tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f) {
+    GraphState* G = (GraphState*)g->graph;
+    if (!G) g->graph = G = new GraphState();
+    if (G->exec && G->y == d_y && G->f == d_f && G->ws == g->ws.base && same_shape(G->p, *p))
+        return TNLM_OK;
+    if (G->exec) {
+        cudaGraphExecDestroy(G->exec);
+        G->exec = nullptr;
+    }
+    if (!G->cap) CK(cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking), "capture stream");
+    long long before[TNLM_KCLASS_COUNT];
+    for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) before[c] = g->launches[c];
+    const unsigned mask = g->prof_mask;
+    g->prof_mask = 0;
+    CK(cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    tnlm_status s = outer_iteration(g, p, d_y, d_f, G->cap);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(G->cap, &graph);
+    g->prof_mask = mask;
+    for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) {
+        G->launches[c] = g->launches[c] - before[c];
+        g->launches[c] = before[c];
+    }
+    if (s != TNLM_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "end capture");
+    const cudaError_t ei = cudaGraphInstantiate(&G->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        G->exec = nullptr;
+        return cuda_fail(ei, "graph instantiate");
+    }
+    G->p = *p;
+    G->y = d_y;
+    G->f = d_f;
+    G->ws = g->ws.base;
     return TNLM_OK;
 }
 
@@ -403,6 +466,12 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
         tnlm_destroy_geometry(g);
         return cuda_fail(e, "geometry table upload");
     }
+    e = prepare_backproject(&g->cta_slots_bp);
+    if (e == cudaSuccess) e = prepare_weights();
+    if (e != cudaSuccess) {
+        tnlm_destroy_geometry(g);
+        return cuda_fail(e, "kernel attributes");
+    }
     *out = g;
     return TNLM_OK;
 }
@@ -415,6 +484,12 @@ void tnlm_destroy_geometry(tnlm_geometry* g) {
     cudaFree(g->d_bin);
     cudaFree(g->d_ray);
     cudaFree(g->ws.base);
+    if (g->graph) {
+        GraphState* G = (GraphState*)g->graph;
+        if (G->exec) cudaGraphExecDestroy(G->exec);
+        if (G->cap) cudaStreamDestroy(G->cap);
+        delete G;
+    }
     if (g->prof) {
         Profiler* P = (Profiler*)g->prof;
         for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
@@ -475,15 +550,18 @@ tnlm_status tnlm_project(const tnlm_geometry* gc, const float* d_img, float* d_s
     return TNLM_OK;
 }
 
-tnlm_status tnlm_backproject(const tnlm_geometry* g, const float* d_sino, float* d_img, void* stream) {
+tnlm_status tnlm_backproject(const tnlm_geometry* gc, const float* d_sino, float* d_img, void* stream) {
     g_err[0] = 0;
-    if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
     if (!d_img || !d_sino) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
     if (!aligned16(d_img) || !aligned16(d_sino)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
     DeviceGuard dg(g->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
-    LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, d_sino, d_img, nullptr, st), "backproject");
+    tnlm_status s = ensure_ws(g, g->ws.base ? g->ws.rho : 0, g->ws.base ? g->ws.kcap : 1, st);
+    if (s != TNLM_OK) return s;
+    LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, d_sino, d_img, nullptr, g->ws.bps, st), "backproject");
     return TNLM_OK;
 }
 
@@ -551,9 +629,21 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* gc, const tnlm_params* p, cons
     LK(TNLM_KCLASS_PREP, launch_sqrt(d_winv, ws.sw, nsg, ws.st.err, st), "sqrt");
     const bool sync = rep != nullptr || p->tol > 0.0;
     int done = 0;
-    for (int k = 0; k < p->k_outer; ++k) {
-        s = outer_iteration(g, p, d_y, d_f, st);
+    // replay a captured iteration unless kernels are being timed individually
+    const bool graphs = g->prof_mask == 0 && p->k_outer > 1;
+    if (graphs) {
+        s = ensure_graph(g, p, d_y, d_f);
         if (s != TNLM_OK) return s;
+    }
+    for (int k = 0; k < p->k_outer; ++k) {
+        if (graphs) {
+            GraphState* G = (GraphState*)g->graph;
+            CK(cudaGraphLaunch(G->exec, st), "graph launch");
+            for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) g->launches[c] += G->launches[c];
+        } else {
+            s = outer_iteration(g, p, d_y, d_f, st);
+            if (s != TNLM_OK) return s;
+        }
         done = k + 1;
         if (p->tol > 0.0 && (done % p->tol_check_every == 0 || done == p->k_outer)) {
             double rel = 0.0;

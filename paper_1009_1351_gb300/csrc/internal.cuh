@@ -58,6 +58,7 @@ struct Workspace {
     float *R = nullptr, *T = nullptr;
     // sinograms
     float *r = nullptr, *z = nullptr, *t = nullptr, *sw = nullptr;
+    float* bps = nullptr;    // backprojection partial images [4][N][ny][nx]
     // TNLM step
     PadPlane pp{};
     float* D = nullptr;      // [N][W*W][py][px]
@@ -82,6 +83,9 @@ struct tnlm_geometry {
     float2* d_bin = nullptr;    // [B] (cos g, sin g)
     float4* d_ray = nullptr;    // [N*V*B] per-ray marching constants (kk, alpha, 1/|kk|, +-L)
     tnlm::Workspace ws;
+    int cta_slots_bp = 0;       // resident backprojector CTAs on the device
+    // CUDA graph of one outer iteration (see api.cu)
+    void* graph = nullptr;
     // profiling: launch counters and event-bracketed timing (see api.cu)
     unsigned prof_mask = 0;
     long long launches[TNLM_KCLASS_COUNT] = {0, 0, 0, 0, 0, 0};
@@ -105,9 +109,13 @@ cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R,
                              cudaStream_t st);
 cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
                            const ProjOut& o, cudaStream_t st);
+cudaError_t prepare_backproject(int* slots);
+cudaError_t prepare_weights();
 int bp_blocks_per_phase(const tnlm_geometry* g);
+size_t bp_scratch_floats(const tnlm_geometry* g);
+// scratch: partial images of the view groups ([4][N][ny][nx]); NULL = one group
 cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float* img,
-                               double* part, cudaStream_t st);
+                               double* part, float* scratch, cudaStream_t st);
 
 // CGLS vector / scalar kernels
 cudaError_t launch_cgls_init_scalars(const tnlm_geometry* g, const Workspace& ws,

@@ -226,31 +226,22 @@ cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* 
 // ---------------------------------------------------------------------------
 constexpr int kBpT = 32;        // tile side
 constexpr int kBpWarps = 8;
+constexpr int kBpMaxGroups = 4;  // view groups per tile (CTAs per tile)
 
 struct BpArgs {
     const float* sino;
-    float* img;
-    double* part;          // nullable: per-block partial sums of img^2
+    float* img;            // output when the tile's views are not split
+    float* scratch;        // [G][N][ny][nx] partial images when they are
+    double* part;          // nullable: per-tile partial sums of img^2
     const float2* view;
     const float4* ray;
-    int nx, ny, V, B;
+    int nx, ny, V, B, G;
     float sidp, inv_dg, half_b;
 };
 
 size_t bp_smem_bytes() {
     return sizeof(float) * (2 * kBpWarps * kBpT * kBpT + kBpT * (kBpT + 1)) +
            sizeof(float4) * kBpWarps * 32;
-}
-
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
 }
 
 // Add frac * Lz to line j and (1 - frac) * Lz to line j + 1 of a private
@@ -263,7 +254,9 @@ __device__ __forceinline__ void deposit(float* acc, float kk, float am, float ik
     if (r0 + 1 >= 0 && r0 + 1 < n) acc[(r0 + 1) * 32] += (1.f - c.frac) * Lz;
 }
 
-template <bool PART>
+// DIRECT: the block sees all views of its tile and writes the image (and the
+// squared-norm partial); otherwise it writes its view group's partial image.
+template <bool DIRECT, bool PART>
 __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
     extern __shared__ float sm[];
     float* accC = sm;                                   // [warp][row][col]
@@ -271,7 +264,8 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
     float* tsum = accR + kBpWarps * kBpT * kBpT;        // [row][col + 1]
     float4* stg = (float4*)(tsum + kBpT * (kBpT + 1));  // [warp][32]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-    const int X0 = blockIdx.x * kBpT, Y0 = blockIdx.y * kBpT, phase = blockIdx.z;
+    const int X0 = blockIdx.x * kBpT, Y0 = blockIdx.y * kBpT;
+    const int phase = blockIdx.z / a.G, grp = blockIdx.z - phase * a.G;
     const int ncols = min(kBpT, a.nx - X0), nrows = min(kBpT, a.ny - Y0);
     for (int k = tid; k < 2 * kBpWarps * kBpT * kBpT; k += blockDim.x) sm[k] = 0.f;
     __syncthreads();
@@ -282,33 +276,69 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
     const float xa = X0 - 0.5f * a.nx, xb = X0 + ncols - 0.5f * a.nx;
     const float ya = Y0 - 0.5f * a.ny, yb = Y0 + nrows - 0.5f * a.ny;
     const unsigned full = 0xffffffffu;
+    const int S = kBpWarps * a.G;              // view stride of a warp
+    const int gw = grp * kBpWarps + w;         // first view of this warp
+    const float4* rays = a.ray + (size_t)phase * a.V * a.B;
+    const float* zs = a.sino + (size_t)phase * a.V * a.B;
+    const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
-    for (int v = w; v < a.V; v += kBpWarps) {
-        const size_t gv = (size_t)phase * a.V + v;
-        const float2 vt = a.view[gv];
-        float bmin = 3e30f, bmax = -3e30f;
-        if (lane < 4) {
-            const float cx = (lane & 1) ? xb : xa, cy = (lane & 2) ? yb : ya;
-            const float X = vt.y * cx - vt.x * cy;
-            const float Y = a.sidp - (vt.x * cx + vt.y * cy);
-            bmin = bmax = fmaf(atanf(X / Y), a.inv_dg, a.half_b);
+    for (int m0 = 0; gw + S * m0 < a.V; m0 += 32) {
+        // bin ranges of the next 32 views of this warp, one view per lane
+        const int vl = gw + S * (m0 + lane);
+        int lo = 1, hi = 0;
+        if (vl < a.V) {
+            const float2 vt = a.view[(size_t)phase * a.V + vl];
+            float bmin = 3e30f, bmax = -3e30f;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float cx = (c & 1) ? xb : xa, cy = (c & 2) ? yb : ya;
+                const float X = vt.y * cx - vt.x * cy;
+                const float Y = a.sidp - (vt.x * cx + vt.y * cy);
+                const float bc = fmaf(atanf(X / Y), a.inv_dg, a.half_b);
+                bmin = fminf(bmin, bc);
+                bmax = fmaxf(bmax, bc);
+            }
+            lo = max(0, (int)floorf(bmin) - 1);
+            hi = min(a.B - 1, (int)ceilf(bmax) + 1);
         }
-        bmin = warp_min(bmin);
-        bmax = warp_max(bmax);
-        const int b_lo = max(0, (int)floorf(bmin) - 1);
-        const int b_hi = min(a.B - 1, (int)ceilf(bmax) + 1);
-        const float4* rays = a.ray + gv * a.B;
-        const float* z = a.sino + gv * a.B;
-        for (int b0 = b_lo; b0 <= b_hi; b0 += 32) {
-            const int nb = min(32, b_hi - b0 + 1);
-            float4 rp = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (lane < nb) rp = __ldg(rays + b0 + lane);
+        const unsigned todo = __ballot_sync(full, lo <= hi);
+        if (!todo) continue;
+        // walk the (view, 32-ray chunk) pairs, prefetching the next chunk's
+        // ray constants and sinogram values while the current one is deposited
+        int vi = __ffs(todo) - 1;
+        int b0 = __shfl_sync(full, lo, vi);
+        int bh = __shfl_sync(full, hi, vi);
+        int nb = min(32, bh - b0 + 1);
+        size_t rb = (size_t)(gw + S * (m0 + vi)) * a.B + b0;
+        float4 rp = lane < nb ? __ldg(rays + rb + lane) : zero4;
+        float zz = lane < nb ? __ldg(zs + rb + lane) : 0.f;
+        while (true) {
+            int nvi = vi, nb0 = b0 + 32, nbh = bh;
+            if (nb0 > bh) {
+                const unsigned rest = todo & ~((2u << vi) - 1u);
+                nvi = rest ? __ffs(rest) - 1 : -1;
+                if (nvi >= 0) {
+                    nb0 = __shfl_sync(full, lo, nvi);
+                    nbh = __shfl_sync(full, hi, nvi);
+                }
+            }
+            int nnb = 0;
+            float4 nrp = zero4;
+            float nzz = 0.f;
+            if (nvi >= 0) {
+                nnb = min(32, nbh - nb0 + 1);
+                const size_t nrb = (size_t)(gw + S * (m0 + nvi)) * a.B + nb0;
+                if (lane < nnb) {
+                    nrp = __ldg(rays + nrb + lane);
+                    nzz = __ldg(zs + nrb + lane);
+                }
+            }
             // bit t: staged ray t marches over columns (L > 0)
             const unsigned colmask = __ballot_sync(full, lane < nb && rp.w > 0.f);
-            const float Lz = lane < nb ? fabsf(rp.w) * __ldg(z + b0 + lane) : 0.f;
             __syncwarp();
-            myS[lane] = make_float4(rp.x, rp.y + fminf(rp.x, 0.f), rp.z, Lz);
+            myS[lane] = make_float4(rp.x, rp.y + fminf(rp.x, 0.f), rp.z, fabsf(rp.w) * zz);
             __syncwarp();
+#pragma unroll 2
             for (int t = 0; t < nb; ++t) {
                 const float4 r = myS[t];
                 if ((colmask >> t) & 1u) {
@@ -317,6 +347,8 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
                     if (lane < nrows) deposit(myR, r.x, r.y, r.z, r.w, Y0 + lane, X0, ncols, a.nx);
                 }
             }
+            if (nvi < 0) break;
+            vi = nvi; b0 = nb0; bh = nbh; nb = nnb; rp = nrp; zz = nzz;
         }
     }
     __syncthreads();
@@ -338,15 +370,17 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
     }
     __syncthreads();
     float sq = 0.f;
+    const int nph = gridDim.z / a.G;
+    float* out = DIRECT ? a.img : a.scratch + (size_t)grp * nph * a.ny * a.nx;
     for (int k = tid; k < kBpT * kBpT; k += blockDim.x) {
         const int r = k >> 5, c = k & 31;
         if (r < nrows && c < ncols) {
             const float v = tsum[r * (kBpT + 1) + c];
-            a.img[((size_t)phase * a.ny + Y0 + r) * a.nx + X0 + c] = v;
+            out[((size_t)phase * a.ny + Y0 + r) * a.nx + X0 + c] = v;
             sq = fmaf(v, v, sq);
         }
     }
-    if (PART) {
+    if (DIRECT && PART) {
         __shared__ double sh[kBpWarps];
         const double tot = block_sum<kBpWarps * 32>(sq, sh, tid);
         if (tid == 0)
@@ -354,31 +388,104 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
     }
 }
 
+// Sum of the G partial images in a fixed order (and the per-tile partials).
+template <bool PART>
+__global__ void __launch_bounds__(256) k_bp_combine(const float* __restrict__ scratch,
+                                                    float* __restrict__ img, double* part,
+                                                    int nx, int ny, int N, int G) {
+    const int X0 = blockIdx.x * kBpT, Y0 = blockIdx.y * kBpT, phase = blockIdx.z;
+    const size_t stride = (size_t)N * nx * ny;
+    float sq = 0.f;
+    for (int k = threadIdx.x; k < kBpT * kBpT; k += blockDim.x) {
+        const int r = k >> 5, c = k & 31;
+        if (Y0 + r < ny && X0 + c < nx) {
+            const size_t idx = ((size_t)phase * ny + Y0 + r) * nx + X0 + c;
+            float v = 0.f;
+            for (int g = 0; g < G; ++g) v += scratch[g * stride + idx];
+            img[idx] = v;
+            sq = fmaf(v, v, sq);
+        }
+    }
+    if (PART) {
+        __shared__ double sh[8];
+        const double tot = block_sum<256>(sq, sh, threadIdx.x);
+        if (threadIdx.x == 0)
+            part[(size_t)phase * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x] = tot;
+    }
+}
+
 int bp_blocks_per_phase(const tnlm_geometry* g) {
     return ((g->nx + kBpT - 1) / kBpT) * ((g->ny + kBpT - 1) / kBpT);
 }
 
+// View groups per tile (CTAs per tile): the smallest G whose grid fills its
+// last wave to >= 85 % (else the best fill), from the occupancy of the
+// kernel and the device's SM count.  Each warp keeps at least one view.
+// Opt the backprojector variants into their dynamic shared memory and
+// count the CTA slots of the current device (called at geometry creation,
+// outside any stream capture).
+cudaError_t prepare_backproject(int* slots) {
+    const int smem = (int)bp_smem_bytes();
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_backproject<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_backproject<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_backproject<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backproject<false, false>,
+                                                           kBpWarps * 32, bp_smem_bytes())) != cudaSuccess)
+        return e;
+    *slots = (sms > 0 && per_sm > 0) ? sms * per_sm : 1;
+    return cudaSuccess;
+}
+
+static int bp_groups(const tnlm_geometry* g) {
+    const int slots = g->cta_slots_bp > 0 ? g->cta_slots_bp : 1;
+    const int tiles = bp_blocks_per_phase(g) * g->N;
+    int best = 1;
+    double best_fill = 0.0;
+    for (int G = 1; G <= kBpMaxGroups && G <= (g->V + kBpWarps - 1) / kBpWarps; ++G) {
+        const long long ctas = (long long)tiles * G;
+        const long long waves = (ctas + slots - 1) / slots;
+        const double fill = (double)ctas / (double)(waves * slots);
+        if (fill >= 0.85) return G;
+        if (fill > best_fill + 1e-9) { best_fill = fill; best = G; }
+    }
+    return best;
+}
+
+size_t bp_scratch_floats(const tnlm_geometry* g) {
+    return (size_t)kBpMaxGroups * g->N * g->nx * g->ny;
+}
+
+template <bool DIRECT, bool PART>
+static cudaError_t launch_bp(const BpArgs& a, dim3 grid, cudaStream_t st) {
+    k_backproject<DIRECT, PART><<<grid, kBpWarps * 32, bp_smem_bytes(), st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float* img,
-                               double* part, cudaStream_t st) {
+                               double* part, float* scratch, cudaStream_t st) {
     BpArgs a;
-    a.sino = sino; a.img = img; a.part = part;
+    a.sino = sino; a.img = img; a.part = part; a.scratch = scratch;
     a.view = g->d_view; a.ray = g->d_ray;
     a.nx = g->nx; a.ny = g->ny; a.V = g->V; a.B = g->B;
+    a.G = scratch ? bp_groups(g) : 1;
     a.sidp = (float)(g->sid / g->pixel);
     a.inv_dg = (float)(g->sdd / g->bin_mm);
     a.half_b = 0.5f * (float)(g->B - 1);
-    dim3 grid((g->nx + kBpT - 1) / kBpT, (g->ny + kBpT - 1) / kBpT, g->N);
-    const size_t smem = bp_smem_bytes();
+    const dim3 tiles((g->nx + kBpT - 1) / kBpT, (g->ny + kBpT - 1) / kBpT, g->N);
+    const dim3 grid(tiles.x, tiles.y, g->N * a.G);
     cudaError_t e;
-    if (part) {
-        e = cudaFuncSetAttribute(k_backproject<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_backproject<true><<<grid, kBpWarps * 32, smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(k_backproject<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        k_backproject<false><<<grid, kBpWarps * 32, smem, st>>>(a);
-    }
+    if (a.G == 1)
+        return part ? launch_bp<true, true>(a, grid, st) : launch_bp<true, false>(a, grid, st);
+    e = launch_bp<false, false>(a, grid, st);
+    if (e != cudaSuccess) return e;
+    if (part)
+        k_bp_combine<true><<<tiles, 256, 0, st>>>(scratch, img, part, g->nx, g->ny, g->N, a.G);
+    else
+        k_bp_combine<false><<<tiles, 256, 0, st>>>(scratch, img, part, g->nx, g->ny, g->N, a.G);
     return cudaGetLastError();
 }
 

@@ -40,15 +40,32 @@ struct WArgs {
     int nx, ny, N, rho, W;
 };
 
+// Shared-memory geometry of k_weights for window radius rho, patch radius R.
+struct WSmem {
+    int GW, GH;   // g tiles (with a spare float4 of columns)
+    int HP, HH;   // horizontal sums: pitch, rows
+    int DR;       // rows of one distance box
+    __host__ __device__ WSmem(int rho, int R) {
+        GW = kWTileX + 2 * (rho + R) + 4;
+        GH = kWTileY + 2 * (rho + R);
+        HP = ((kWTileX + rho + 4) + 3) / 4 * 4;
+        HH = kWTileY + rho + 2 * R + 4;
+        DR = kWTileY + rho + 4;
+    }
+    __host__ __device__ size_t floats() const {
+        return 2 * (size_t)GW * GH + (size_t)HP * HH + 2 * (size_t)HP * DR;
+    }
+};
+
 template <int R>
 __global__ void __launch_bounds__(256) k_weights(WArgs a) {
     extern __shared__ float sm[];
     const int rho = a.rho, W = a.W;
-    const int GW = kWTileX + 2 * (rho + R), GH = kWTileY + 2 * (rho + R);
-    const int HW = kWTileX + rho, HH = kWTileY + rho + 2 * R;
+    const WSmem L(rho, R);
     float* Gi = sm;
-    float* Gj = Gi + GW * GH;
-    float* Hb = Gj + GW * GH;
+    float* Gj = Gi + L.GW * L.GH;
+    float* H = Gj + L.GW * L.GH;
+    float* Db = H + L.HP * L.HH;              // two distance boxes
     const int p = blockIdx.z, j = (p + 1) % a.N;
     const int X0 = blockIdx.x * kWTileX, Y0 = blockIdx.y * kWTileY;
     const int gx0 = X0 - rho - R, gy0 = Y0 - rho - R;
@@ -57,12 +74,13 @@ __global__ void __launch_bounds__(256) k_weights(WArgs a) {
     const size_t npx = (size_t)nx * ny;
     const float* gp = a.g + p * npx;
     const float* gq = a.g + j * npx;
-    for (int e = tid; e < GW * GH; e += 256) {
-        const int x = gx0 + e % GW, y = gy0 + e / GW;
+    for (int e = tid; e < L.GW * L.GH; e += 256) {
+        const int x = gx0 + e % L.GW, y = gy0 + e / L.GW;
         const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
         Gi[e] = in ? gp[(size_t)y * nx + x] : 0.f;
         Gj[e] = in ? gq[(size_t)y * nx + x] : 0.f;
     }
+    for (int e = tid; e < L.HP * L.HH; e += 256) H[e] = 0.f;
     const int tx = tid & 31, ty = tid >> 5;
     if (a.U0) {  // padded copy of g_p: u^(0) of the Gauss-Jacobi sweeps
         for (int kk = 0; kk < 2; ++kk) {
@@ -80,49 +98,65 @@ __global__ void __launch_bounds__(256) k_weights(WArgs a) {
     for (int sy = -rho; sy <= rho; ++sy) {
         for (int sx = -rho; sx <= rho; ++sx) {
             const int k = (sy + rho) * W + (sx + rho);
-            float* H = Hb + (k & 1) * HW * HH;
+            float* D = Db + (k & 1) * L.HP * L.DR;
+            // box = bounding box of the tile and of the tile shifted by -s
             const int bw = kWTileX + abs(sx), bh = kWTileY + abs(sy);
             const int ox = X0 + min(0, -sx), oy = Y0 + min(0, -sy);
-            const int nrow = bh + 2 * R;
-            // horizontal patch sums over the box, rows widened by r
-            for (int e = tid; e < bw * nrow; e += 256) {
-                const int cx = e % bw, cr = e / bw;
-                const int zx = ox + cx, zy = oy + cr - R;
-                const float* pi = Gi + (zy - gy0) * GW + (zx - gx0);
-                const float* pj = Gj + (zy + sy - gy0) * GW + (zx + sx - gx0);
-                float h = 0.f;
+            // (1) horizontal patch sums, 4 adjacent box columns per task, on
+            //     box rows widened by r: H(c, r') = sum_q d2(c + q, r' - R)
+            const int ncg = (bw + 3) / 4, nrow = bh + 2 * R;
+            for (int e = tid; e < ncg * nrow; e += 256) {
+                const int cg = e % ncg, cr = e / ncg;
+                const int zx = ox + 4 * cg - R, zy = oy + cr - R;   // leftmost tap
+                const float* pi = Gi + (zy - gy0) * L.GW + (zx - gx0);
+                const float* pj = Gj + (zy + sy - gy0) * L.GW + (zx + sx - gx0);
+                float d2[4 + 2 * R];
 #pragma unroll
-                for (int q = -R; q <= R; ++q) {
+                for (int q = 0; q < 4 + 2 * R; ++q) {
                     const float d = pi[q] - pj[q];
-                    h = fmaf(d, d, h);
+                    d2[q] = d * d;
                 }
-                H[cr * HW + cx] = h;
+                float h[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int q = 0; q <= 2 * R; ++q) t += d2[c + q];
+                    h[c] = t;
+                }
+                *(float4*)(H + cr * L.HP + 4 * cg) = make_float4(h[0], h[1], h[2], h[3]);
             }
             __syncthreads();
-            // vertical sums for this thread's pixels: forward (x) and backward (x - s)
+            // (2) vertical sums, 4 adjacent box rows per task: D(c, r) = sum_q H(c, r + q)
+            const int nrg = (bh + 3) / 4;
+            for (int e = tid; e < bw * nrg; e += 256) {
+                const int c = e % bw, rg = e / bw;
+                float hv[4 + 2 * R];
+#pragma unroll
+                for (int q = 0; q < 4 + 2 * R; ++q) hv[q] = H[(4 * rg + q) * L.HP + c];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    float t = 0.f;
+#pragma unroll
+                    for (int q = 0; q <= 2 * R; ++q) t += hv[r + q];
+                    D[(4 * rg + r) * L.HP + c] = t;
+                }
+            }
+            __syncthreads();
+            // (3) forward distance (stored) and backward row minimum of this thread's pixels
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
                 const int x = X0 + tx, y = Y0 + ty + 8 * kk;
                 const bool in = x < nx && y < ny;
-                {
-                    const int cx = x - ox, cr = y - oy;
-                    float d = 0.f;
-#pragma unroll
-                    for (int q = 0; q <= 2 * R; ++q) d += H[(cr + q) * HW + cx];
-                    const bool valid = in && x + sx >= 0 && x + sx < nx && y + sy >= 0 && y + sy < ny;
-                    if (in)
-                        Dp[(size_t)k * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] =
-                            valid ? d : INFINITY;
-                    if (valid) mf[kk] = fminf(mf[kk], d);
-                }
-                {
-                    const int cx = x - sx - ox, cr = y - sy - oy;
-                    float d = 0.f;
-#pragma unroll
-                    for (int q = 0; q <= 2 * R; ++q) d += H[(cr + q) * HW + cx];
-                    const bool valid = in && x - sx >= 0 && x - sx < nx && y - sy >= 0 && y - sy < ny;
-                    if (valid) mb[kk] = fminf(mb[kk], d);
-                }
+                const float df = D[(y - oy) * L.HP + (x - ox)];
+                const bool vf = in && x + sx >= 0 && x + sx < nx && y + sy >= 0 && y + sy < ny;
+                if (in)
+                    Dp[(size_t)k * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] =
+                        vf ? df : INFINITY;
+                if (vf) mf[kk] = fminf(mf[kk], df);
+                const float db = D[(y - sy - oy) * L.HP + (x - sx - ox)];
+                const bool vb = in && x - sx >= 0 && x - sx < nx && y - sy >= 0 && y - sy < ny;
+                if (vb) mb[kk] = fminf(mb[kk], db);
             }
         }
     }
@@ -138,18 +172,25 @@ __global__ void __launch_bounds__(256) k_weights(WArgs a) {
     }
 }
 
-static size_t weights_smem(int rho, int R) {
-    const int GW = kWTileX + 2 * (rho + R), GH = kWTileY + 2 * (rho + R);
-    const int HW = kWTileX + rho, HH = kWTileY + rho + 2 * R;
-    return sizeof(float) * (2 * (size_t)GW * GH + 2 * (size_t)HW * HH);
+static size_t weights_smem(int rho, int R) { return sizeof(float) * WSmem(rho, R).floats(); }
+
+// Opt every weight-kernel variant into the largest dynamic shared memory any
+// window can need (called at geometry creation, outside any stream capture).
+cudaError_t prepare_weights() {
+    cudaError_t e = cudaSuccess;
+#define TNLM_PREP_W(R)                                                                  \
+    if (e == cudaSuccess)                                                               \
+        e = cudaFuncSetAttribute(k_weights<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)weights_smem((kMaxWindow - 1) / 2, R));
+    TNLM_PREP_W(0) TNLM_PREP_W(1) TNLM_PREP_W(2) TNLM_PREP_W(3)
+    TNLM_PREP_W(4) TNLM_PREP_W(5) TNLM_PREP_W(6) TNLM_PREP_W(7)
+#undef TNLM_PREP_W
+    return e;
 }
 
 template <int R>
 static cudaError_t launch_weights_r(const WArgs& a, cudaStream_t st) {
     const size_t smem = weights_smem(a.rho, R);
-    cudaError_t e = cudaFuncSetAttribute(k_weights<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((a.nx + kWTileX - 1) / kWTileX, (a.ny + kWTileY - 1) / kWTileY, a.N);
     k_weights<R><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();

@@ -299,3 +299,25 @@ def test_mid_size_reconstruction_matches_oracle(tn, oracle_mod):
     p = synth.Params(**{**c.params.__dict__, "k_outer": 3})
     got, ref, rep, rel, res = run_both(tn, oracle_mod, c.geom, d, p, np.full((10, 256, 256), 0.01))
     assert rel_l2(got, ref) <= REC_TOL
+
+
+def test_graph_replay_matches_eager_launches(tn, tiny_case):
+    """With kernel timing on, iterations are launched one kernel at a time;
+    otherwise a captured CUDA graph of one iteration is replayed.  Both must
+    give bitwise the same result, and the launch counters must agree."""
+    c, d, f0 = tiny_case
+    geo = tn.tnlm_create_geometry(c.geom)
+    y, w = dev(d["y"]), dev(d["w"])
+    a, b = dev(f0), dev(f0)
+    tn.tnlm_reconstruct(geo, c.params, y, w, dev(f0))      # workspace set-up, graph capture
+    tn.tnlm_profile_read(geo)
+    tn.tnlm_reconstruct(geo, c.params, y, w, a)            # graph replay
+    n_graph = tn.tnlm_profile_read(geo)
+    tn.tnlm_profile_enable(geo, ("gj",))
+    tn.tnlm_reconstruct(geo, c.params, y, w, b)            # eager
+    n_eager = tn.tnlm_profile_read(geo)
+    tn.tnlm_profile_enable(geo, ())
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert {k: v["launches"] for k, v in n_graph.items()} == {k: v["launches"] for k, v in n_eager.items()}
+    assert n_eager["gj"]["ms"] > 0
