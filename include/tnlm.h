@@ -115,6 +115,28 @@ void tnlm_destroy_geometry(tnlm_geometry* geom);
 tnlm_status tnlm_project(const tnlm_geometry* geom, const float* d_img, float* d_sino,
                          void* stream);
 
+/* Same result as tnlm_project, for callers that cannot allocate device
+ * memory: code that runs while a CUDA stream capture is open, applications
+ * whose device memory is fixed at start-up or fully owned by another
+ * allocator, and hosts that only hand out preallocated buffers.  (This call
+ * has no counterpart in the paper.)  tnlm_project keeps its layout copies in
+ * the handle's workspace, which is sized for a whole reconstruction and
+ * allocated on first use; this variant allocates nothing: its scratch is a
+ * file-scope device array of 6 Mi floats (24 MiB) that every GPU which loads
+ * the library holds until the process exits.
+ *   - Limit: N * (ny * (nx + 4) + nx * (ny + 4)) floats plus alignment must fit
+ *     in 6 Mi floats (e.g. 10 phases of 512 x 512); larger geometries return
+ *     TNLM_ERR_INVALID_ARG and nothing is launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (each call clears the part it uses before filling it).  Calls whose
+ *     work overlaps on the GPU (other streams or threads) race on it.
+ * Arguments, layouts and the other errors are those of tnlm_project. */
+tnlm_status tnlm_project_static(const tnlm_geometry* geom, const float* d_img, float* d_sino,
+                                void* stream);
+
 /* d_img[i] = P_i^T d_sino[i] (the adjoint used by the CGLS box and Eq. 4):
  * the exact transpose of tnlm_project, computed as an atomic-free gather.
  * In: sinogram [N][V][B]; out: image [N][ny][nx], overwritten. */

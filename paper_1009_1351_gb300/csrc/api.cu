@@ -550,6 +550,34 @@ tnlm_status tnlm_project(const tnlm_geometry* gc, const float* d_img, float* d_s
     return TNLM_OK;
 }
 
+tnlm_status tnlm_project_static(const tnlm_geometry* gc, const float* d_img, float* d_sino,
+                                void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    if (!d_img || !d_sino) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_img) || !aligned16(d_sino)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
+    // row-major and column-major padded copies of the image, back to back
+    const size_t nR = align_up((size_t)g->N * g->ny * (g->nx + 4), 64);
+    const size_t nT = (size_t)g->N * g->nx * (g->ny + 4);
+    if (nR + nT > static_scratch_floats())
+        return fail(TNLM_ERR_INVALID_ARG,
+                    "image too large for the static scratch: needs %zu floats, the array holds %zu",
+                    nR + nT, static_scratch_floats());
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    float* base = nullptr;
+    CK(static_scratch_ptr(&base), "cudaGetSymbolAddress");
+    // the array keeps the previous call's contents: the zero pads are restored
+    CK(cudaMemsetAsync(base, 0, sizeof(float) * (nR + nT), st), "scratch clear");
+    LK(TNLM_KCLASS_PREP, launch_prep_dual(g, d_img, base, base + nR, st), "prep");
+    ProjOut o{};
+    o.mode = 0; o.q = d_sino;
+    LK(TNLM_KCLASS_PROJECT, launch_project(g, base, base + nR, o, st), "project");
+    return TNLM_OK;
+}
+
 tnlm_status tnlm_backproject(const tnlm_geometry* gc, const float* d_sino, float* d_img, void* stream) {
     g_err[0] = 0;
     if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;

@@ -112,6 +112,8 @@ cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* 
 cudaError_t prepare_backproject(int* slots);
 cudaError_t prepare_weights();
 int bp_blocks_per_phase(const tnlm_geometry* g);
+size_t static_scratch_floats();
+cudaError_t static_scratch_ptr(float** out);
 size_t bp_scratch_floats(const tnlm_geometry* g);
 // scratch: partial images of the view groups ([4][N][ny][nx]); NULL = one group
 cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float* img,

@@ -34,6 +34,8 @@
 
 #include <math.h>
 
+#include <mutex>
+
 namespace tnlm {
 
 // ---------------------------------------------------------------------------
@@ -487,6 +489,36 @@ cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float*
     else
         k_bp_combine<false><<<tiles, 256, 0, st>>>(scratch, img, part, g->nx, g->ny, g->N, a.G);
     return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free projection: the dual-layout scratch of K1 lives in a
+// file-scope device array instead of the handle's workspace.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchFloats = (size_t)6 << 20;   // 24 MiB per device
+static __device__ __align__(256) float g_proj_scratch[kStaticScratchFloats];
+
+size_t static_scratch_floats() { return kStaticScratchFloats; }
+
+// Device address of the array on the current device.  In host code the
+// symbol is only a host-side stand-in, so the address is looked up with
+// cudaGetSymbolAddress once per device (with that device current) and cached.
+cudaError_t static_scratch_ptr(float** out) {
+    static std::mutex mu;
+    static float* ptrs[64] = {nullptr};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_proj_scratch);
+        if (e != cudaSuccess) return e;
+        ptrs[dev] = (float*)p;
+    }
+    *out = ptrs[dev];
+    return cudaSuccess;
 }
 
 }  // namespace tnlm
