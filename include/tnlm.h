@@ -143,6 +143,18 @@ tnlm_status tnlm_project_static(const tnlm_geometry* geom, const float* d_img, f
 tnlm_status tnlm_backproject(const tnlm_geometry* geom, const float* d_sino, float* d_img,
                              void* stream);
 
+/* Initial image f^(0) of the TNLM algorithm box (step 1: reconstruction by
+ * FBP from all projections of all N phases).  The paper does not name the
+ * filter; this is equiangular fan-beam FBP: each projection is weighted by
+ * sid*cos(g), convolved with the discrete ramp kernel c(0) = 1/(8 dg^2),
+ * c(odd n) = -1/(2 pi^2 sin^2(n dg)), c(even n) = 0 (dg = bin_mm / sdd_mm),
+ * and backprojected with weight (2 pi / (N V)) / L^2, L the source-pixel
+ * distance, reading the filtered projection by linear interpolation.  It
+ * assumes the N*V views cover 360 degrees evenly.
+ * In: d_y [N][V][B] line integrals; out: d_img [N][ny][nx], every phase the
+ * same image.  Uses the handle's workspace (allocated on first use). */
+tnlm_status tnlm_fbp(const tnlm_geometry* geom, const float* d_y, float* d_img, void* stream);
+
 /* Byte sizes of the two output buffers of tnlm_weights. */
 tnlm_status tnlm_weights_size(const tnlm_geometry* geom, const tnlm_params* params,
                               size_t* dist_bytes, size_t* norm_bytes);

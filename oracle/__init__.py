@@ -188,3 +188,12 @@ def objective_op(G: Geom, y, w, f, wnext, W: int, mu: float) -> float:
     """Data term of Eq. 1 plus mu * sum_i [||f_i||^2 - <f_i, W_{i,i+1} f_{i+1}>]."""
     return float(_load().orc_objective_op(*G.args(), _d(_f64(y)), _d(_f64(w)), _d(_f64(f)),
                                           _d(_f64(wnext)), ctypes.c_int(W), ctypes.c_double(mu)))
+
+
+def fbp(G: Geom, y) -> np.ndarray:
+    """Initial image of the TNLM algorithm box (step 1): fan-beam FBP of all
+    phases' projections together (equiangular form, discrete ramp kernel);
+    every phase receives the same image."""
+    f = np.zeros(G.img_shape)
+    _load().orc_fbp(*G.args(), _d(_f64(y).reshape(G.sino_shape)), _d(f))
+    return f

@@ -20,6 +20,7 @@
  *       (sum over y of omega = 1), search window of Sec. 2.3.
  *   orc_gj                          the Gauss-Jacobi box of Sec. 2.2.
  *   orc_reconstruct                 the TNLM algorithm box of Sec. 2.2.
+ *   orc_fbp                         step 1 of the TNLM box: FBP of all views
  *   orc_objective_op                data term of Eq. 1 plus the TNLM energy
  *       whose exact prox the Gauss-Jacobi fixed point (Eq. 7) is.
  *
@@ -56,6 +57,8 @@
 #define BINW gd[1]
 #define SID  gd[2]
 #define SDD  gd[3]
+
+static const double ORC_PI = 3.14159265358979323846;
 
 int orc_threads(int n)
 {
@@ -499,4 +502,76 @@ double orc_objective_op(const int* gi, const double* gd, const double* ang,
     }
     free(t);
     return data + mu * reg;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initial image (TNLM algorithm box, step 1): filtered backprojection of    */
+/* the projections of all N phases together, for the equiangular arc        */
+/* detector.  The paper does not name the filter; this is the textbook       */
+/* equiangular fan-beam FBP with the unwindowed discrete ramp kernel:        */
+/*   R'(g_k)  = R(g_k) * sid * cos(g_k)                                     */
+/*   Q(g_n)   = dg * sum_k R'(g_k) c(n - k),                                 */
+/*              c(0) = 1/(8 dg^2), c(even) = 0, c(odd n) = -1/(2 pi^2 sin^2(n dg)) */
+/*   f(x)     = sum_views dbeta * Q(g'(x)) / L(x)^2,  dbeta = 2 pi / (N V)   */
+/* with g'(x) the fan angle of x, L its distance to the source, and Q read   */
+/* by linear interpolation (zero beyond the detector).  Every phase of the   */
+/* output receives the same image.                                          */
+/* ------------------------------------------------------------------------ */
+void orc_fbp(const int* gi, const double* gd, const double* ang, const double* y, double* f)
+{
+    const int B = NB;
+    const long M = (long)NPH * NV;
+    const double dg = BINW / SDD;
+    const double dbeta = 2.0 * ORC_PI / (double)M;
+    const long npx = (long)NX * NY;
+    double* Q = (double*)malloc(sizeof(double) * M * B);
+    double* c = (double*)malloc(sizeof(double) * (2 * B - 1));
+    for (int n = -(B - 1); n <= B - 1; ++n) {
+        double v;
+        if (n == 0) v = 1.0 / (8.0 * dg * dg);
+        else if (n % 2 == 0) v = 0.0;
+        else {
+            double s = sin(n * dg);
+            v = -1.0 / (2.0 * ORC_PI * ORC_PI * s * s);
+        }
+        c[n + B - 1] = v;
+    }
+#pragma omp parallel for schedule(static)
+    for (long v = 0; v < M; ++v) {
+        for (int n = 0; n < B; ++n) {
+            double acc = 0.0;
+            for (int k = 0; k < B; ++k) {
+                double gk = ((double)k - 0.5 * (B - 1)) * dg;
+                acc += y[v * B + k] * SID * cos(gk) * c[n - k + B - 1];
+            }
+            Q[v * B + n] = dg * acc;
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < npx; ++p) {
+        int ix = (int)(p % NX), iy = (int)(p / NX);
+        double px_ = ((double)ix - 0.5 * (NX - 1)) * PIX;
+        double py_ = ((double)iy - 0.5 * (NY - 1)) * PIX;
+        double acc = 0.0;
+        for (long v = 0; v < M; ++v) {
+            double th = ang[v];
+            double sx = SID * cos(th), sy = SID * sin(th);
+            double cx = -cos(th), cy = -sin(th);           /* central ray */
+            double dx = px_ - sx, dy = py_ - sy;
+            double along = cx * dx + cy * dy;               /* dot(c, p - S) */
+            double across = cx * dy - cy * dx;              /* cross(c, p - S) */
+            double gam = atan2(across, along);
+            double u = gam / dg + 0.5 * (B - 1);
+            int k0 = (int)floor(u);
+            double t = u - k0;
+            double q = 0.0;
+            if (k0 >= 0 && k0 < B) q += (1.0 - t) * Q[v * B + k0];
+            if (k0 + 1 >= 0 && k0 + 1 < B) q += t * Q[v * B + k0 + 1];
+            acc += q / (dx * dx + dy * dy);
+        }
+        acc *= dbeta;
+        for (int i = 0; i < NPH; ++i) f[(long)i * npx + p] = acc;
+    }
+    free(Q);
+    free(c);
 }

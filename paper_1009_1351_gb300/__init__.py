@@ -29,7 +29,7 @@ TNLM_DATA_GRAD = 1
 EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tnlm_backproject",
             "tnlm_weights_size", "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct",
             "tnlm_last_error", "tnlm_debug_fail_alloc_after", "tnlm_profile_enable",
-            "tnlm_profile_read", "tnlm_project_static")
+            "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp")
 KCLASSES = ("prep", "project", "backproject", "cgls", "weights", "gj")
 
 
@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_project.argtypes = [vp, vp, vp, vp]
     lib.tnlm_backproject.argtypes = [vp, vp, vp, vp]
     lib.tnlm_project_static.argtypes = [vp, vp, vp, vp]
+    lib.tnlm_fbp.argtypes = [vp, vp, vp, vp]
     lib.tnlm_weights_size.argtypes = [vp, ctypes.POINTER(ParamsC), ctypes.POINTER(ctypes.c_size_t),
                                       ctypes.POINTER(ctypes.c_size_t)]
     lib.tnlm_weights.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp, vp]
@@ -92,7 +93,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_profile_enable.argtypes = [vp, ctypes.c_uint]
     lib.tnlm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
-    for name in ("tnlm_create_geometry", "tnlm_project", "tnlm_project_static", "tnlm_backproject",
+    for name in ("tnlm_create_geometry", "tnlm_project", "tnlm_project_static", "tnlm_fbp",
+                 "tnlm_backproject",
                  "tnlm_weights_size",
                  "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct", "tnlm_profile_enable",
                  "tnlm_profile_read"):
@@ -189,6 +191,11 @@ def tnlm_project(geom: Geometry, img, sino, stream=None) -> None:
 def tnlm_project_static(geom: Geometry, img, sino, stream=None) -> None:
     """tnlm_project without any device allocation (fixed-size static scratch)."""
     _check(load_library().tnlm_project_static(geom.handle, _ptr(img), _ptr(sino), _stream(stream)))
+
+
+def tnlm_fbp(geom: Geometry, y, img, stream=None) -> None:
+    """Initial image: fan-beam FBP of all phases' projections (every phase the same)."""
+    _check(load_library().tnlm_fbp(geom.handle, _ptr(y), _ptr(img), _stream(stream)))
 
 
 def tnlm_backproject(geom: Geometry, sino, img, stream=None) -> None:

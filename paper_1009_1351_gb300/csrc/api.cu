@@ -151,11 +151,12 @@ WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
     const size_t nsg = (size_t)g->V * g->B;
     // interior starts at a 16-byte aligned column with one spare float4 beyond
     // the window radius on each side (vectorised Gauss-Jacobi windows)
+    // and whole 64 x 16 Gauss-Jacobi tiles inside every plane
     const int ox = (int)align_up((size_t)rho, 4) + 4;
     L.pp.ox = ox;
     L.pp.oy = rho;
-    L.pp.px = (int)align_up((size_t)g->nx, 4) + 2 * ox;
-    L.pp.py = g->ny + 2 * rho;
+    L.pp.px = (int)align_up((size_t)g->nx, 64) + 2 * ox;
+    L.pp.py = (int)align_up((size_t)g->ny, 16) + 2 * rho;
     L.pp.plane = (size_t)L.pp.px * L.pp.py;
     const size_t W2 = (size_t)(2 * rho + 1) * (2 * rho + 1);
     size_t o = 0;
@@ -447,21 +448,35 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
             hr[v * g->B + b] = make_float4((float)kk, (float)alpha, (float)ik, (float)L);
         }
     }
-    void *pv = nullptr, *pb = nullptr, *pr = nullptr;
+    // taps of the discrete equiangular ramp kernel (initial FBP)
+    std::vector<float> ht(2 * (size_t)g->B - 1);
+    for (int n = -(g->B - 1); n <= g->B - 1; ++n) {
+        double v = 0.0;
+        if (n == 0) v = 1.0 / (8.0 * dg_ * dg_);
+        else if (n % 2 != 0) {
+            const double sn = sin(n * dg_);
+            v = -1.0 / (2.0 * 9.8696044010893586188 * sn * sn);   // pi^2
+        }
+        ht[n + g->B - 1] = (float)v;
+    }
+    void *pv = nullptr, *pb = nullptr, *pr = nullptr, *pt = nullptr;
     cudaError_t e = dev_alloc(&pv, sizeof(float2) * NV);
     if (e == cudaSuccess) e = dev_alloc(&pb, sizeof(float2) * g->B);
     if (e == cudaSuccess) e = dev_alloc(&pr, sizeof(float4) * NV * g->B);
+    if (e == cudaSuccess) e = dev_alloc(&pt, sizeof(float) * ht.size());
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(pv); cudaFree(pb); cudaFree(pr);
+        cudaFree(pv); cudaFree(pb); cudaFree(pr); cudaFree(pt);
         delete g;
         return fail(e == cudaErrorMemoryAllocation ? TNLM_ERR_OOM : TNLM_ERR_CUDA,
                     "geometry table allocation failed: %s", cudaGetErrorString(e));
     }
     g->d_view = (float2*)pv; g->d_bin = (float2*)pb; g->d_ray = (float4*)pr;
+    g->d_fbp_taps = (float*)pt;
     e = cudaMemcpy(pv, hv.data(), sizeof(float2) * NV, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pb, hb.data(), sizeof(float2) * g->B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pr, hr.data(), sizeof(float4) * NV * g->B, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pt, ht.data(), sizeof(float) * ht.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         tnlm_destroy_geometry(g);
         return cuda_fail(e, "geometry table upload");
@@ -483,6 +498,7 @@ void tnlm_destroy_geometry(tnlm_geometry* g) {
     cudaFree(g->d_view);
     cudaFree(g->d_bin);
     cudaFree(g->d_ray);
+    cudaFree(g->d_fbp_taps);
     cudaFree(g->ws.base);
     if (g->graph) {
         GraphState* G = (GraphState*)g->graph;
@@ -590,6 +606,21 @@ tnlm_status tnlm_backproject(const tnlm_geometry* gc, const float* d_sino, float
     tnlm_status s = ensure_ws(g, g->ws.base ? g->ws.rho : 0, g->ws.base ? g->ws.kcap : 1, st);
     if (s != TNLM_OK) return s;
     LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, d_sino, d_img, nullptr, g->ws.bps, st), "backproject");
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_fbp(const tnlm_geometry* gc, const float* d_y, float* d_img, void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    if (!d_y || !d_img) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_y) || !aligned16(d_img)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    tnlm_status s = ensure_ws(g, g->ws.base ? g->ws.rho : 0, g->ws.base ? g->ws.kcap : 1, st);
+    if (s != TNLM_OK) return s;
+    LK(TNLM_KCLASS_PREP, launch_fbp(g, d_y, g->ws.t, d_img, st), "fbp");
     return TNLM_OK;
 }
 

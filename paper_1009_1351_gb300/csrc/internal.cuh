@@ -82,6 +82,7 @@ struct tnlm_geometry {
     float2* d_view = nullptr;   // [N*V] (cos t, sin t)
     float2* d_bin = nullptr;    // [B] (cos g, sin g)
     float4* d_ray = nullptr;    // [N*V*B] per-ray marching constants (kk, alpha, 1/|kk|, +-L)
+    float* d_fbp_taps = nullptr; // [2B-1] discrete equiangular ramp kernel of the initial FBP
     tnlm::Workspace ws;
     int cta_slots_bp = 0;       // resident backprojector CTAs on the device
     // CUDA graph of one outer iteration (see api.cu)
@@ -118,6 +119,10 @@ size_t bp_scratch_floats(const tnlm_geometry* g);
 // scratch: partial images of the view groups ([4][N][ny][nx]); NULL = one group
 cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float* img,
                                double* part, float* scratch, cudaStream_t st);
+
+// initial image (filtered backprojection of all views); Q: [N*V*B] scratch
+cudaError_t launch_fbp(const tnlm_geometry* g, const float* y, float* Q, float* img,
+                       cudaStream_t st);
 
 // CGLS vector / scalar kernels
 cudaError_t launch_cgls_init_scalars(const tnlm_geometry* g, const Workspace& ws,

@@ -248,12 +248,18 @@ size_t bp_smem_bytes() {
 
 // Add frac * Lz to line j and (1 - frac) * Lz to line j + 1 of a private
 // accumulator column (tile-local index j relative to j0, n lines).
+// The lower line index here is not clamped into [-1, nacross] as in K1: the
+// two lines that receive a deposit lie inside the tile and the image, where
+// that clamp leaves the index unchanged, so every deposited entry is the one
+// K1 forms.
 __device__ __forceinline__ void deposit(float* acc, float kk, float am, float ik, float Lz,
-                                        int k, int j0, int n, int nacross) {
-    const Cut c = line_cut(kk, am, ik, (float)k, (float)nacross);
-    const int r0 = c.j - j0;
-    if (r0 >= 0 && r0 < n) acc[r0 * 32] += c.frac * Lz;
-    if (r0 + 1 >= 0 && r0 + 1 < n) acc[(r0 + 1) * 32] += (1.f - c.frac) * Lz;
+                                        float kf, int j0, unsigned n) {
+    const float mn = fmaf(kk, kf, am);
+    const float fl = floorf(mn);
+    const float frac = fminf(1.f, fmaf(fl - mn, ik, ik));
+    const int r0 = (__float_as_int(fl + 12582912.f) - 0x4B400000) - j0;
+    if ((unsigned)r0 < n) acc[r0 * 32] += frac * Lz;
+    if ((unsigned)(r0 + 1) < n) acc[(r0 + 1) * 32] += fmaf(-frac, Lz, Lz);
 }
 
 // DIRECT: the block sees all views of its tile and writes the image (and the
@@ -278,6 +284,7 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
     const float xa = X0 - 0.5f * a.nx, xb = X0 + ncols - 0.5f * a.nx;
     const float ya = Y0 - 0.5f * a.ny, yb = Y0 + nrows - 0.5f * a.ny;
     const unsigned full = 0xffffffffu;
+    const float kfc = (float)(X0 + lane), kfr = (float)(Y0 + lane);  // this lane's column / row
     const int S = kBpWarps * a.G;              // view stride of a warp
     const int gw = grp * kBpWarps + w;         // first view of this warp
     const float4* rays = a.ray + (size_t)phase * a.V * a.B;
@@ -344,9 +351,9 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
             for (int t = 0; t < nb; ++t) {
                 const float4 r = myS[t];
                 if ((colmask >> t) & 1u) {
-                    if (lane < ncols) deposit(myC, r.x, r.y, r.z, r.w, X0 + lane, Y0, nrows, a.ny);
+                    if (lane < ncols) deposit(myC, r.x, r.y, r.z, r.w, kfc, Y0, (unsigned)nrows);
                 } else {
-                    if (lane < nrows) deposit(myR, r.x, r.y, r.z, r.w, Y0 + lane, X0, ncols, a.nx);
+                    if (lane < nrows) deposit(myR, r.x, r.y, r.z, r.w, kfr, X0, (unsigned)ncols);
                 }
             }
             if (nvi < 0) break;

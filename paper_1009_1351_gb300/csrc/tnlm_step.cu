@@ -46,9 +46,12 @@ struct WSmem {
     int HP, HH;   // horizontal sums: pitch, rows
     int DR;       // rows of one distance box
     __host__ __device__ WSmem(int rho, int R) {
-        GW = kWTileX + 2 * (rho + R) + 4;
+        // odd pitch: lanes on consecutive rows hit distinct banks
+        GW = (kWTileX + 2 * (rho + R) + 4) | 1;
         GH = kWTileY + 2 * (rho + R);
+        // pitch/4 odd: float4 stores of consecutive rows hit distinct bank groups
         HP = ((kWTileX + rho + 4) + 3) / 4 * 4;
+        if (((HP / 4) & 1) == 0) HP += 4;
         HH = kWTileY + rho + 2 * R + 4;
         DR = kWTileY + rho + 4;
     }
@@ -106,7 +109,7 @@ __global__ void __launch_bounds__(256) k_weights(WArgs a) {
             //     box rows widened by r: H(c, r') = sum_q d2(c + q, r' - R)
             const int ncg = (bw + 3) / 4, nrow = bh + 2 * R;
             for (int e = tid; e < ncg * nrow; e += 256) {
-                const int cg = e % ncg, cr = e / ncg;
+                const int cr = e % nrow, cg = e / nrow;     // rows fastest: conflict-free
                 const int zx = ox + 4 * cg - R, zy = oy + cr - R;   // leftmost tap
                 const float* pi = Gi + (zy - gy0) * L.GW + (zx - gx0);
                 const float* pj = Gj + (zy + sy - gy0) * L.GW + (zx + sx - gx0);
@@ -477,7 +480,10 @@ cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int win
     a.g = gimg; a.uin = uin; a.uout = uout; a.fout = fout; a.clamp = clamp;
     // the partial slots not written by this launch must read as zero
     const int nv = gjv_blocks(g), ns = gjs_blocks(g);
-    if (ws.pp.ox >= ((a.rho + 3) / 4) * 4 + 4 && (ws.pp.px % 4) == 0 &&
+    const int tw = kGjvTx * kGjvPx;
+    const int tx64 = (g->nx + tw - 1) / tw * tw, ty16 = (g->ny + kGjvTy - 1) / kGjvTy * kGjvTy;
+    if (ws.pp.ox >= ((a.rho + 3) / 4) * 4 + 4 && ws.pp.oy >= a.rho && (ws.pp.px % 4) == 0 &&
+        ws.pp.px >= tx64 + 2 * ws.pp.ox && ws.pp.py >= ty16 + 2 * ws.pp.oy &&
         (fout ? launch_gj_vec<1>(a, window, nv, st) : launch_gj_vec<0>(a, window, nv, st))) {
         if (fout && ns > nv) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nv, 0, 16 * (size_t)(ns - nv), st);
         return cudaGetLastError();

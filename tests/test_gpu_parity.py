@@ -321,3 +321,39 @@ def test_graph_replay_matches_eager_launches(tn, tiny_case):
     assert torch.equal(a, b)
     assert {k: v["launches"] for k, v in n_graph.items()} == {k: v["launches"] for k, v in n_eager.items()}
     assert n_eager["gj"]["ms"] > 0
+
+
+@pytest.mark.parametrize("W,d", [(3, 1), (9, 3), (13, 5), (15, 7), (17, 3)])
+def test_gauss_jacobi_window_sizes_match_oracle(tn, oracle_mod, W, d):
+    """Weights + 2 sweeps (m1 = 0) on a ragged 3-phase image for every
+    compiled window size (and one above them, which takes the generic sweep)."""
+    g = synth.Geometry(nx=83, ny=45, pixel_mm=1.0, n_phases=3, n_views=6, n_bins=64,
+                       bin_mm=1.2, sid_mm=500.0, sdd_mm=800.0)
+    G = oracle_mod.Geom(g)
+    rng = np.random.default_rng(W)
+    base = 0.02 * rng.random((g.ny, g.nx))
+    f0 = np.stack([np.roll(base, k, axis=0) + 0.001 * rng.random((g.ny, g.nx)) for k in range(3)])
+    y = np.zeros(G.sino_shape)
+    w = np.ones(G.sino_shape)
+    p = synth.Params(mu_hat=0.7, h=0.002 * d, patch=d, window=W, m1=0, m2=2, k_outer=1, clamp=0)
+    got, ref, rep, rel, res = run_both(tn, oracle_mod, g, {"y": y, "w": w}, p, f0)
+    assert rel_l2(got, ref) <= OP_TOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged", "mid_c"])
+def test_fbp_initial_image_matches_oracle(tn, oracle_mod, name):
+    """Step 1 of the TNLM algorithm box: FBP of all phases' projections."""
+    g = GEOMS[name] if name in GEOMS else synth.case(name).geom
+    G = oracle_mod.Geom(g)
+    if name == "ragged":
+        y = oracle_mod.project(G, 0.02 * np.random.default_rng(2).random(G.img_shape))
+    else:
+        y = synth.make_inputs(synth.case(name))["y"]
+    y = y.astype(np.float32).astype(np.float64)
+    ref = oracle_mod.fbp(G, y)
+    geo = tn.tnlm_create_geometry(g)
+    out = torch.zeros(G.img_shape, device="cuda")
+    tn.tnlm_fbp(geo, dev(y), out)
+    got = host(out)
+    assert rel_l2(got, ref) <= 2e-5
+    assert all(np.array_equal(got[0], got[i]) for i in range(1, g.n_phases))

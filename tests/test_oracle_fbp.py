@@ -1,0 +1,63 @@
+"""Pins of the oracle's initial image (TNLM algorithm box, step 1: FBP of
+the projections of all phases together).
+
+The fan-beam FBP inverts exact line integrals of a uniform disc: inside the
+disc it returns the disc's attenuation, outside zero, with an error that
+shrinks as the views, bins and pixels are refined.
+"""
+import numpy as np
+import pytest
+
+from paper_1009_1351_gb300 import synth
+
+
+def disc_case(L, V, B, fov=64.0, cx=5.0, cy=-3.0, R=18.0, mu=0.02, N=3):
+    pix = fov / L
+    g = synth.Geometry(nx=L, ny=L, pixel_mm=pix, n_phases=N, n_views=V, n_bins=B,
+                       bin_mm=fov * 1.2 / B * 1.5, sid_mm=500.0, sdd_mm=750.0)
+    src, d = synth.ray_endpoints(g)
+    p = np.abs((src[..., 0] - cx) * d[..., 1] - (src[..., 1] - cy) * d[..., 0])
+    y = 2.0 * mu * np.sqrt(np.maximum(R * R - p * p, 0.0))
+    xs = (np.arange(L) - (L - 1) / 2) * pix
+    X, Y = np.meshgrid(xs, xs)
+    r = np.hypot(X - cx, Y - cy)
+    return g, y, r, mu, R
+
+
+def disc_errors(oracle_mod, L, V, B):
+    g, y, r, mu, R = disc_case(L, V, B)
+    f = oracle_mod.fbp(oracle_mod.Geom(g), y)
+    inner = f[0][r < R - 4 * g.pixel_mm]
+    outer = f[0][(r > R + 4 * g.pixel_mm) & (r < 28.0)]
+    return abs(inner.mean() - mu) / mu, np.abs(outer).mean() / mu, inner.std() / mu, f
+
+
+def test_fbp_recovers_a_uniform_disc(oracle_mod):
+    bias, out, noise, f = disc_errors(oracle_mod, 64, 120, 128)
+    assert bias < 0.01
+    assert out < 0.02
+    assert noise < 0.02
+
+
+def test_fbp_gives_every_phase_the_same_image(oracle_mod):
+    g, y, r, mu, R = disc_case(32, 60, 64)
+    f = oracle_mod.fbp(oracle_mod.Geom(g), y)
+    assert np.array_equal(f[0], f[1]) and np.array_equal(f[0], f[2])
+
+
+def test_fbp_error_shrinks_with_refinement(oracle_mod):
+    coarse = disc_errors(oracle_mod, 32, 60, 64)
+    fine = disc_errors(oracle_mod, 64, 180, 192)
+    # interior bias and spread shrink; the exterior residue is the ringing of
+    # the unwindowed ramp kernel at the disc edge and is pinned separately
+    assert fine[0] < 0.6 * coarse[0]
+    assert fine[2] < 0.6 * coarse[2]
+
+
+def test_fbp_is_linear(oracle_mod):
+    g = synth.small_geometry(nx=12, ny=12, V=10, B=24)
+    G = oracle_mod.Geom(g)
+    rng = np.random.default_rng(4)
+    a, b = rng.random(G.sino_shape), rng.random(G.sino_shape)
+    fa, fb, fab = oracle_mod.fbp(G, a), oracle_mod.fbp(G, b), oracle_mod.fbp(G, 2 * a - 3 * b)
+    np.testing.assert_allclose(fab, 2 * fa - 3 * fb, rtol=1e-10, atol=1e-12)
