@@ -241,6 +241,7 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     ws.st.iter = si + N;
     ws.st.err = si + N + 1;
     // zero everything (pads of R/T, halos of U0/U1, state), then +inf in D
+    ws.tm_ok = encode_distance_maps(ws, g->N);
     CK(cudaMemsetAsync(base, 0, L.total, st), "workspace clear");
     LK(TNLM_KCLASS_PREP, launch_fill(ws.D, INFINITY, (L.off_U0 - L.off_D) / 4, st), "distance halo fill");
     return TNLM_OK;

@@ -15,6 +15,7 @@
 //   partials      FP64 per-block sums, reduced in a fixed order (deterministic)
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -71,6 +72,14 @@ struct Workspace {
     size_t part_len = 0;
     double* part2 = nullptr; // second partial array (relative change)
     DevState st{};
+    // TMA descriptors of the distance planes [N*W2max][py][px]: boxes of
+    // 64 x 16 (forward rows) and 68 x 16 (backward rows) floats
+    alignas(64) CUtensorMap tmF{};
+    alignas(64) CUtensorMap tmB{};
+    // and of the Gauss-Jacobi iterates U0 / U1 [N][py][px]: box 80 x 30
+    alignas(64) CUtensorMap tmU0{};
+    alignas(64) CUtensorMap tmU1{};
+    bool tm_ok = false;
 };
 
 }  // namespace tnlm
@@ -153,6 +162,8 @@ cudaError_t launch_weights_norm(const tnlm_geometry* g, const Workspace& ws, int
                                 double h, cudaStream_t st);
 cudaError_t launch_weights_export(const tnlm_geometry* g, const Workspace& ws, int window,
                                   float* d_dist, float* d_norm, cudaStream_t st);
+// encode ws.tmF / ws.tmB for the distance planes (false if TMA is unavailable)
+bool encode_distance_maps(Workspace& ws, int N);
 
 // ---- device helpers -------------------------------------------------------
 __device__ __forceinline__ float warp_sum(float v) {

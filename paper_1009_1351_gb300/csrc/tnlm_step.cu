@@ -177,6 +177,8 @@ __global__ void __launch_bounds__(256) k_weights(WArgs a) {
 
 static size_t weights_smem(int rho, int R) { return sizeof(float) * WSmem(rho, R).floats(); }
 
+static cudaError_t prepare_gj_tma();
+
 // Opt every weight-kernel variant into the largest dynamic shared memory any
 // window can need (called at geometry creation, outside any stream capture).
 cudaError_t prepare_weights() {
@@ -188,7 +190,7 @@ cudaError_t prepare_weights() {
     TNLM_PREP_W(0) TNLM_PREP_W(1) TNLM_PREP_W(2) TNLM_PREP_W(3)
     TNLM_PREP_W(4) TNLM_PREP_W(5) TNLM_PREP_W(6) TNLM_PREP_W(7)
 #undef TNLM_PREP_W
-    return e;
+    return e == cudaSuccess ? prepare_gj_tma() : e;
 }
 
 template <int R>
@@ -431,6 +433,330 @@ __global__ void __launch_bounds__(kGjvTx * kGjvTy) k_gj_vec(GjArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-pipelined sweep (W in {3, 5, ..., 15}).  A block owns a 64 x 16 pixel
+// tile of one phase: 8 consumer warps (a thread owns 4 consecutive pixels of
+// one row) and one producer warp.  For every window shift the producer
+// loads two boxes of the distance planes with tensor-map copies
+// (cp.async.bulk.tensor): the 64 x 16 forward box of pair i at the tile and
+// the 68 x 16 backward box of pair i-1 at the tile shifted by -s (x rounded
+// down to a 16-byte boundary), into a ring of stages.  Each stage has a
+// "full" mbarrier (expected bytes) and an "empty" one (one arrival per
+// consumer warp); every wait is bounded and a timeout ends the block with an
+// error flag after draining its copies.
+// ---------------------------------------------------------------------------
+constexpr int kTmaTW = 64, kTmaTH = 16;
+constexpr int kTmaBW = kTmaTW + 4;
+constexpr int kTmaConsumers = 256;
+constexpr int kTmaThreads = kTmaConsumers + 32;
+constexpr int kTmaStageFloats = kTmaTH * (kTmaTW + kTmaBW);   // 2112 floats = 66 x 128 B
+constexpr int kTmaStages = 6;
+constexpr long kTmaSpinLimit = 1L << 24;
+// neighbour-phase tile: the 64 x 16 pixels widened by 8 columns and 7 rows
+// on each side (every window up to 15 x 15), loaded once per block
+constexpr int kTmaUW = kTmaTW + 16, kTmaUH = kTmaTH + 14;
+constexpr int kTmaUFloats = kTmaUW * kTmaUH;    // 2400 floats = 75 x 128 B
+
+struct TmaMaps {
+    CUtensorMap F, B, U;     // forward / backward distance boxes, iterate tile box
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    for (long it = 0; it < kTmaSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(kTmaThreads) k_gj_tma(GjArgs a, const __grid_constant__ CUtensorMap tmF,
+                                                        const __grid_constant__ CUtensorMap tmB,
+                                                        const __grid_constant__ CUtensorMap tmU) {
+    constexpr int RHO = (W - 1) / 2;
+    constexpr int UOFF = 4 * ((RHO + 3) / 4);
+    constexpr int UW = 4 + 2 * UOFF;
+    constexpr int NK = W * W;
+    extern __shared__ __align__(128) float tma_sm_raw[];
+    // tensor-copy destinations must be 128-byte aligned: round the base up
+    float* stages = (float*)(((uintptr_t)tma_sm_raw + 127) & ~(uintptr_t)127);
+    float* utile = stages + kTmaStages * kTmaStageFloats;          // [2][kTmaUH][kTmaUW]
+    uint64_t* full = (uint64_t*)(utile + 2 * kTmaUFloats);
+    uint64_t* empty = full + kTmaStages;
+    uint64_t* ubar = empty + kTmaStages;
+    __shared__ int s_abort, s_issued;
+    __shared__ double wsum[2][kTmaConsumers / 32];
+    const int N = a.N, nx = a.nx, ny = a.ny;
+    const int tile = blockIdx.x / N, i = blockIdx.x % N;
+    const int tilesx = (nx + kTmaTW - 1) / kTmaTW;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int X0 = (tile % tilesx) * kTmaTW, Y0 = (tile / tilesx) * kTmaTH;
+    const int ip = (i + N - 1) % N, inx = (i + 1) % N;
+    const int px = a.pp.px;
+    const size_t plane = a.pp.plane;
+    if (tid == 0) {
+        for (int st = 0; st < kTmaStages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], kTmaConsumers / 32);
+        }
+        mbar_init(ubar, 1);
+        s_abort = 0;
+        s_issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == kTmaConsumers / 32) {
+        if (lane == 0) {   // producer
+            // the two neighbour-phase tiles (rows/columns outside the plane read 0)
+            mbar_arrive_expect_tx(ubar, 8u * kTmaUFloats);
+            tma_load_3d(utile, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, inx, ubar);
+            tma_load_3d(utile + kTmaUFloats, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, ip, ubar);
+            int k = 0;
+            for (; k < NK; ++k) {
+                const int slot = k % kTmaStages;
+                if (k >= kTmaStages &&
+                    !mbar_wait_bounded(&empty[slot], (unsigned)((k / kTmaStages - 1) & 1))) {
+                    s_abort = 1;
+                    break;
+                }
+                if (*(volatile int*)&s_abort) break;
+                const int dy = k / W - RHO, dx = k % W - RHO;
+                const int off = -dx;
+                const int base = off >= 0 ? (off / 4) * 4 : -(((-off) + 3) / 4) * 4;
+                float* stg = stages + slot * kTmaStageFloats;
+                mbar_arrive_expect_tx(&full[slot], 4u * kTmaStageFloats);
+                tma_load_3d(stg, &tmF, X0 + a.pp.ox, Y0 + a.pp.oy, i * NK + k, &full[slot]);
+                tma_load_3d(stg + kTmaTH * kTmaTW, &tmB, X0 + a.pp.ox + base, Y0 + a.pp.oy - dy,
+                            ip * NK + k, &full[slot]);
+            }
+            s_issued = k;
+        }
+    } else {
+        const int tx = tid % 16, ty = tid / 16;
+        const int x0 = X0 + 4 * tx, y = Y0 + ty;
+        const bool rowin = x0 < nx && y < ny;
+        const size_t npx = (size_t)nx * ny;
+        float af[4] = {0.f, 0.f, 0.f, 0.f}, zf[4] = {0.f, 0.f, 0.f, 0.f};
+        float ab[4] = {0.f, 0.f, 0.f, 0.f}, zb[4] = {0.f, 0.f, 0.f, 0.f};
+        const float k2 = a.k2;
+        float mfk[4], mbk[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const bool in = rowin && x0 + p < nx;
+            const size_t pix = (size_t)y * nx + x0 + p;
+            mfk[p] = in ? a.mins[i * npx + pix] * k2 : 0.f;
+            mbk[p] = in ? a.mins[(N + i) * npx + pix] * k2 : 0.f;
+        }
+        // window rows of this thread inside the neighbour tiles
+        const float* Un = utile + (ty + 7) * kTmaUW + 4 * tx + 8 - UOFF;
+        const float* Up = utile + kTmaUFloats + (ty + 7) * kTmaUW + 4 * tx + 8 - UOFF;
+        bool ok = mbar_wait_bounded(ubar, 0u);
+        if (!ok) s_abort = 1;
+        int k = 0;
+        for (int sy = 0; sy < W && ok; ++sy) {
+            const int dy = sy - RHO;
+            float un[UW], up[UW];
+#pragma unroll
+            for (int q = 0; q < UW / 4; ++q) {
+                const float4 vn = *((const float4*)(Un + dy * kTmaUW) + q);
+                const float4 vp = *((const float4*)(Up - dy * kTmaUW) + q);
+                un[4 * q] = vn.x; un[4 * q + 1] = vn.y; un[4 * q + 2] = vn.z; un[4 * q + 3] = vn.w;
+                up[4 * q] = vp.x; up[4 * q + 1] = vp.y; up[4 * q + 2] = vp.z; up[4 * q + 3] = vp.w;
+            }
+#pragma unroll
+            for (int sx = 0; sx < W; ++sx, ++k) {
+                const int dx = sx - RHO;
+                const int slot = k % kTmaStages;
+                if (!mbar_wait_bounded(&full[slot], (unsigned)((k / kTmaStages) & 1))) {
+                    s_abort = 1;
+                    ok = false;
+                    break;
+                }
+                const float* stg = stages + slot * kTmaStageFloats;
+                const float4 f4 = *(const float4*)(stg + ty * kTmaTW + 4 * tx);
+                const int off = -dx;
+                const int base = off >= 0 ? (off / 4) * 4 : -(((-off) + 3) / 4) * 4;
+                const int sh = off - base;
+                const float* pb = stg + kTmaTH * kTmaTW + ty * kTmaBW + 4 * tx;
+                const float4 b0 = *(const float4*)pb;
+                const float4 b1 = *(const float4*)(pb + 4);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the stage
+                const float df[4] = {f4.x, f4.y, f4.z, f4.w};
+                const float w8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    const float ef = ex2_approx(fmaf(-df[p], k2, mfk[p]));
+                    const float eb = ex2_approx(fmaf(-w8[sh + p], k2, mbk[p]));
+                    af[p] = fmaf(ef, un[UOFF + p + dx], af[p]);
+                    ab[p] = fmaf(eb, up[UOFF + p - dx], ab[p]);
+                    zf[p] += ef;
+                    zb[p] += eb;
+                }
+            }
+        }
+        if (ok) {
+            float dsq = 0.f, nsq = 0.f;
+            bool bad = false;
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const int x = x0 + p;
+                if (!rowin || x >= nx) continue;
+                bad |= !(zf[p] >= 0.5f) || !(zb[p] >= 0.5f);
+                const size_t pix = (size_t)y * nx + x;
+                const float unew = fmaf(a.g[i * npx + pix], a.c1, a.c2 * (af[p] / zf[p] + ab[p] / zb[p]));
+                if (MODE == 0) {
+                    a.uout[i * plane + (size_t)(y + a.pp.oy) * px + x + a.pp.ox] = unew;
+                } else {
+                    const float fnew = a.clamp ? fmaxf(unew, 0.f) : unew;
+                    const float fold = a.fout[i * npx + pix];
+                    a.fout[i * npx + pix] = fnew;
+                    dsq = fmaf(fnew - fold, fnew - fold, dsq);
+                    nsq = fmaf(fnew, fnew, nsq);
+                }
+            }
+            if (bad) atomicOr(a.err, 8);
+            if (MODE == 1) {
+                const float d = warp_sum(dsq), n = warp_sum(nsq);
+                if (lane == 0) {
+                    wsum[0][warp] = (double)d;
+                    wsum[1][warp] = (double)n;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (s_abort) {
+        if (tid == 0) {
+            atomicOr(a.err, 16);
+            mbar_wait_bounded(ubar, 0u);
+            for (int kk = s_issued - kTmaStages; kk < s_issued; ++kk)   // drain copies in flight
+                if (kk >= 0) mbar_wait_bounded(&full[kk % kTmaStages], (unsigned)((kk / kTmaStages) & 1));
+        }
+        __syncthreads();
+        return;
+    }
+    if (MODE == 1 && tid == 0) {
+        double d2 = 0.0, n2 = 0.0;
+        for (int w = 0; w < kTmaConsumers / 32; ++w) {
+            d2 += wsum[0][w];
+            n2 += wsum[1][w];
+        }
+        a.part[2 * (size_t)blockIdx.x] = d2;
+        a.part[2 * (size_t)blockIdx.x + 1] = n2;
+    }
+}
+
+static size_t tma_smem() {
+    return 128 + sizeof(float) * (kTmaStages * kTmaStageFloats + 2 * kTmaUFloats) + 16 * kTmaStages + 8;
+}
+
+// Opt the TMA sweeps into their dynamic shared memory (geometry creation).
+static cudaError_t prepare_gj_tma() {
+    const int sm = (int)tma_smem();
+    cudaError_t e = cudaSuccess;
+#define TNLM_PREP_GJ(W)                                                                     \
+    if (e == cudaSuccess)                                                                   \
+        e = cudaFuncSetAttribute(k_gj_tma<W, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); \
+    if (e == cudaSuccess)                                                                   \
+        e = cudaFuncSetAttribute(k_gj_tma<W, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    TNLM_PREP_GJ(3) TNLM_PREP_GJ(5) TNLM_PREP_GJ(7) TNLM_PREP_GJ(9) TNLM_PREP_GJ(11)
+    TNLM_PREP_GJ(13) TNLM_PREP_GJ(15)
+#undef TNLM_PREP_GJ
+    return e;
+}
+
+template <int MODE>
+static bool launch_gj_tma(const GjArgs& a, const Workspace& ws, int window, int nb, cudaStream_t st) {
+    const size_t sm = tma_smem();
+    const CUtensorMap* U = a.uin == ws.U0 ? &ws.tmU0 : (a.uin == ws.U1 ? &ws.tmU1 : nullptr);
+    if (!U) return false;
+    switch (window) {
+        case 3: k_gj_tma<3, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        case 5: k_gj_tma<5, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        case 7: k_gj_tma<7, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        case 9: k_gj_tma<9, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        case 11: k_gj_tma<11, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        case 13: k_gj_tma<13, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        case 15: k_gj_tma<15, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        default: return false;
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool encode_distance_maps(Workspace& ws, int N) {
+    static EncodeTiledFn fn = nullptr;
+    static bool looked = false;
+    if (!looked) {
+        looked = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+        else
+            cudaGetLastError();
+    }
+    if (!fn || !ws.D || !ws.U0 || !ws.U1) return false;
+    const int W2 = (2 * ws.rho + 1) * (2 * ws.rho + 1);
+    const cuuint64_t dims[3] = {(cuuint64_t)ws.pp.px, (cuuint64_t)ws.pp.py, (cuuint64_t)N * W2};
+    const cuuint64_t strides[2] = {(cuuint64_t)ws.pp.px * 4, (cuuint64_t)ws.pp.plane * 4};
+    const cuuint32_t boxF[3] = {kTmaTW, kTmaTH, 1}, boxB[3] = {kTmaBW, kTmaTH, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    if (fn(&ws.tmF, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ws.D, dims, strides, boxF, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    if (fn(&ws.tmB, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ws.D, dims, strides, boxB, es,
+           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    const cuuint64_t udims[3] = {(cuuint64_t)ws.pp.px, (cuuint64_t)ws.pp.py, (cuuint64_t)N};
+    const cuuint32_t boxU[3] = {kTmaUW, kTmaUH, 1};
+    for (int b = 0; b < 2; ++b)
+        if (fn(b ? &ws.tmU1 : &ws.tmU0, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, b ? ws.U1 : ws.U0, udims,
+               strides, boxU, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    return true;
+}
+
 static int gjv_blocks(const tnlm_geometry* g) {
     const int tx = (g->nx + kGjvTx * kGjvPx - 1) / (kGjvTx * kGjvPx);
     const int ty = (g->ny + kGjvTy - 1) / kGjvTy;
@@ -482,6 +808,14 @@ cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int win
     const int nv = gjv_blocks(g), ns = gjs_blocks(g);
     const int tw = kGjvTx * kGjvPx;
     const int tx64 = (g->nx + tw - 1) / tw * tw, ty16 = (g->ny + kGjvTy - 1) / kGjvTy * kGjvTy;
+    const bool layout_ok = ws.pp.ox >= ((a.rho + 3) / 4) * 4 + 4 && ws.pp.oy >= a.rho &&
+                           (ws.pp.px % 4) == 0 && ws.pp.px >= tx64 + 2 * ws.pp.ox &&
+                           ws.pp.py >= ty16 + 2 * ws.pp.oy;
+    if (layout_ok && ws.tm_ok &&
+        (fout ? launch_gj_tma<1>(a, ws, window, nv, st) : launch_gj_tma<0>(a, ws, window, nv, st))) {
+        if (fout && ns > nv) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nv, 0, 16 * (size_t)(ns - nv), st);
+        return cudaGetLastError();
+    }
     if (ws.pp.ox >= ((a.rho + 3) / 4) * 4 + 4 && ws.pp.oy >= a.rho && (ws.pp.px % 4) == 0 &&
         ws.pp.px >= tx64 + 2 * ws.pp.ox && ws.pp.py >= ty16 + 2 * ws.pp.oy &&
         (fout ? launch_gj_vec<1>(a, window, nv, st) : launch_gj_vec<0>(a, window, nv, st))) {
