@@ -49,7 +49,7 @@ typedef enum {
     TNLM_ERR_OOM = 2,         /* device workspace allocation failed (nothing leaked) */
     TNLM_ERR_CUDA = 3,        /* a CUDA runtime call failed */
     TNLM_ERR_NUMERIC = 4,     /* a non-finite value was met in the weights or images */
-    TNLM_ERR_TIMEOUT = 5      /* reserved for bounded device waits */
+    TNLM_ERR_TIMEOUT = 5      /* a bounded device-side wait (TMA pipeline of the sweep) ran out */
 } tnlm_status;
 
 enum { TNLM_DETECTOR_ARC = 0 };

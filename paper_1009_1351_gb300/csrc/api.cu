@@ -735,6 +735,8 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* gc, const tnlm_params* p, cons
         }
         if (err) {
             CK(cudaMemsetAsync(ws.st.err, 0, sizeof(int), st), "reset");
+            if (err & 16)   // a bounded wait of the TMA sweep ran out
+                return fail(TNLM_ERR_TIMEOUT, "a device-side wait timed out (flags 0x%x)", err);
             return fail(TNLM_ERR_NUMERIC, "non-finite value met on the device (flags 0x%x)", err);
         }
     }

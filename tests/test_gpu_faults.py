@@ -80,7 +80,8 @@ def test_injected_allocation_failure_reports_oom_and_recovers(tn, case):
     geo.close()
     geo2.close()
     torch.cuda.synchronize()
-    assert abs(torch.cuda.mem_get_info()[0] - free0) < (4 << 20)
+    # nothing leaked (free memory may also grow when the driver trims its caches)
+    assert free0 - torch.cuda.mem_get_info()[0] < (4 << 20)
 
 
 def test_nonfinite_input_raises_numeric(tn, case):
