@@ -195,6 +195,40 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* geom, const tnlm_params* param
                              const float* d_y, const float* d_winv, float* d_f,
                              tnlm_report* rep, void* stream);
 
+/* Launch autotuner (the paper has no counterpart; it chooses how the same
+ * arithmetic is laid out on the device).  Runs one outer iteration of the
+ * algorithm box from d_f0 on a scratch copy (d_f0 is not modified), then
+ * times the backprojection with 1..4 view groups (CTAs) per 32 x 32 tile and
+ * the Gauss-Jacobi sweep with 1..3 pixel tiles per CTA, and keeps the
+ * fastest choice in the handle (used by every later call on it).  Results
+ * are cached per device and shape (nx, ny, N, V, B, window, patch): a second
+ * handle of the same shape is tuned without timing.  The choice changes
+ * launch shapes only: the sweep's tiling leaves results bitwise unchanged;
+ * the number of view groups changes the order in which the FP32
+ * backprojection sums its views, so results may differ in the last bits
+ * (each choice is deterministic).  Synchronises the stream; allocates one image-sized scratch
+ * buffer for the duration of the call.  bp_groups / gj_tiles (may be NULL)
+ * receive the choice.  Errors: as tnlm_reconstruct. */
+tnlm_status tnlm_autotune(tnlm_geometry* geom, const tnlm_params* params, const float* d_y,
+                          const float* d_winv, const float* d_f0, int* bp_groups, int* gj_tiles,
+                          void* stream);
+
+/* Batched reconstruction of many independent slices (each its own handle,
+ * sizes, view counts and parameters may differ; all on one device).  Each
+ * slice runs exactly params[i].k_outer outer iterations of the algorithm box
+ * (tol must be 0) from d_f[i], as tnlm_reconstruct would, with bitwise the
+ * same result.  One outer iteration of all slices is captured as one CUDA
+ * graph with a branch per slice and replayed once per iteration on the
+ * stream, so kernels of different slices overlap; slices that reach their
+ * k_outer leave the graph.  autotune_shapes != 0 runs tnlm_autotune first
+ * on every handle not yet tuned.  reports (may be NULL) is an array of
+ * count reports.  Synchronises the stream.  Errors: as tnlm_reconstruct; the
+ * first failing slice's status is returned after all reports are filled. */
+tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_params* params,
+                                   int count, const float* const* d_y, const float* const* d_winv,
+                                   float* const* d_f, tnlm_report* reports, int autotune_shapes,
+                                   void* stream);
+
 /* Kernel classes, for launch counting and optional device timing. */
 enum {
     TNLM_KCLASS_PREP = 0,        /* layout copies, fills, sqrt(Sigma^{-1}) */

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
-from typing import Any, Dict, Optional, Tuple
+from typing import Any, Dict, List, Optional, Tuple
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libtnlm.so")
@@ -29,7 +29,8 @@ TNLM_DATA_GRAD = 1
 EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tnlm_backproject",
             "tnlm_weights_size", "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct",
             "tnlm_last_error", "tnlm_debug_fail_alloc_after", "tnlm_profile_enable",
-            "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp")
+            "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp", "tnlm_autotune",
+            "tnlm_reconstruct_batch")
 KCLASSES = ("prep", "project", "backproject", "cgls", "weights", "gj")
 
 
@@ -87,6 +88,11 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_workspace_bytes.argtypes = [vp, ctypes.POINTER(ParamsC), ctypes.POINTER(ctypes.c_size_t)]
     lib.tnlm_reconstruct.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp,
                                      ctypes.POINTER(ReportC), vp]
+    lib.tnlm_autotune.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp, ctypes.POINTER(ctypes.c_int),
+                                  ctypes.POINTER(ctypes.c_int), vp]
+    lib.tnlm_reconstruct_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ParamsC), ctypes.c_int,
+                                           ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                           ctypes.POINTER(ReportC), ctypes.c_int, vp]
     lib.tnlm_last_error.restype = ctypes.c_char_p
     lib.tnlm_debug_fail_alloc_after.argtypes = [ctypes.c_int]
     lib.tnlm_debug_fail_alloc_after.restype = None
@@ -243,6 +249,51 @@ def tnlm_reconstruct(geom: Geometry, params, y, winv, f, report: bool = True,
     n = rep.iterations
     return {"iterations": n, "rel_change": rep.rel_change, "data_residual": rep.data_residual,
             "rel_change_hist": list(rel[:n]), "residual_hist": list(res[:n])}
+
+
+def tnlm_autotune(geom: Geometry, params, y, winv, f0, stream=None) -> Dict[str, int]:
+    """Measure and keep the fastest launch shapes for this handle (f0 is not
+    modified).  Returns {"bp_groups": G, "gj_tiles": T}."""
+    pc = params_c(params)
+    bg, gt = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load_library().tnlm_autotune(geom.handle, ctypes.byref(pc), _ptr(y), _ptr(winv), _ptr(f0),
+                                        ctypes.byref(bg), ctypes.byref(gt), _stream(stream)))
+    return {"bp_groups": bg.value, "gj_tiles": gt.value}
+
+
+def tnlm_reconstruct_batch(geoms, params, ys, winvs, fs, autotune: bool = True,
+                           stream=None) -> List[Dict[str, Any]]:
+    """Run the TNLM iteration in place on every f of the batch (one CUDA
+    graph per outer iteration for all slices).  params: one parameter set or
+    one per slice (fixed k_outer, tol = 0).  Returns one report per slice."""
+    n = len(geoms)
+    if not (len(ys) == len(winvs) == len(fs) == n):
+        raise ValueError("geoms, ys, winvs and fs must have the same length")
+    plist = list(params) if isinstance(params, (list, tuple)) else [params] * n
+    if len(plist) != n:
+        raise ValueError("one parameter set per slice expected")
+    pcs = (ParamsC * n)(*[params_c(p) for p in plist])
+    vp = ctypes.c_void_p
+    hs = (vp * n)(*[g.handle for g in geoms])
+    yp = (vp * n)(*[_ptr(t) for t in ys])
+    wp = (vp * n)(*[_ptr(t) for t in winvs])
+    fp = (vp * n)(*[_ptr(t) for t in fs])
+    hist = []
+    reps = (ReportC * n)()
+    for k in range(n):
+        kk = max(int(pcs[k].k_outer), 1)
+        rel, res = (ctypes.c_double * kk)(), (ctypes.c_double * kk)()
+        hist.append((rel, res))
+        reps[k] = ReportC(0, 0.0, 0.0, rel, res)
+    _check(load_library().tnlm_reconstruct_batch(hs, pcs, n, yp, wp, fp, reps, 1 if autotune else 0,
+                                                 _stream(stream)))
+    out = []
+    for k in range(n):
+        m = reps[k].iterations
+        out.append({"iterations": m, "rel_change": reps[k].rel_change,
+                    "data_residual": reps[k].data_residual,
+                    "rel_change_hist": list(hist[k][0][:m]), "residual_hist": list(hist[k][1][:m])})
+    return out
 
 
 def tnlm_debug_fail_alloc_after(n: int) -> None:

@@ -8,7 +8,10 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <array>
 #include <atomic>
+#include <map>
+#include <mutex>
 #include <vector>
 
 using namespace tnlm;
@@ -313,6 +316,7 @@ struct GraphState {
     const float* y = nullptr;
     float* f = nullptr;
     void* ws = nullptr;
+    unsigned tune_gen = 0;
     long long launches[TNLM_KCLASS_COUNT] = {0, 0, 0, 0, 0, 0};  // kernels per replay
 };
 
@@ -325,7 +329,8 @@ bool same_shape(const tnlm_params& a, const tnlm_params& b) {
 tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f) {
     GraphState* G = (GraphState*)g->graph;
     if (!G) g->graph = G = new GraphState();
-    if (G->exec && G->y == d_y && G->f == d_f && G->ws == g->ws.base && same_shape(G->p, *p))
+    if (G->exec && G->y == d_y && G->f == d_f && G->ws == g->ws.base && same_shape(G->p, *p) &&
+        G->tune_gen == g->tune_gen)
         return TNLM_OK;
     if (G->exec) {
         cudaGraphExecDestroy(G->exec);
@@ -360,6 +365,254 @@ tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_
     G->y = d_y;
     G->f = d_f;
     G->ws = g->ws.base;
+    G->tune_gen = g->tune_gen;
+    return TNLM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner: measures the launch choices of the two kernels whose best shape
+// depends on the device and the workload -- the number of view groups (CTAs)
+// per backprojection tile and the number of tiles per CTA of the TMA sweep --
+// and keeps the fastest.  Results are cached per device and shape.
+// ---------------------------------------------------------------------------
+std::atomic<unsigned long long> g_uid{1};
+std::mutex g_tune_mu;
+std::map<std::array<int, 8>, std::array<int, 2>> g_tune_cache;
+
+std::array<int, 8> tune_key(const tnlm_geometry* g, const tnlm_params* p) {
+    return {g->device, g->nx, g->ny, g->N, g->V, g->B, p->window, p->patch};
+}
+
+void set_tuning(tnlm_geometry* g, int bp_groups, int gj_tpb) {
+    if (g->tune_bp_groups != bp_groups || g->tune_gj_tpb != gj_tpb || g->tune_gen == 0) {
+        g->tune_bp_groups = bp_groups;
+        g->tune_gj_tpb = gj_tpb;
+        g->tune_gen++;
+    }
+}
+
+// Device time (ms) of one call of fn, the median-free mean of 'reps' calls
+// after one warm-up call.
+template <class F>
+tnlm_status time_calls(cudaStream_t st, int reps, F fn, float* ms) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a), "event");
+    cudaError_t e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(a);
+        return cuda_fail(e, "event");
+    }
+    e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) e = fn();
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+    *ms = t / reps;
+    return TNLM_OK;
+}
+
+tnlm_status autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y, const float* d_winv,
+                     const float* d_f0, cudaStream_t st) {
+    const std::array<int, 8> key = tune_key(g, p);
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            set_tuning(g, it->second[0], it->second[1]);
+            return TNLM_OK;
+        }
+    }
+    tnlm_status s = ensure_ws(g, (p->window - 1) / 2, p->k_outer < 1 ? 1 : p->k_outer, st);
+    if (s != TNLM_OK) return s;
+    Workspace& ws = g->ws;
+    const size_t nimg = (size_t)g->N * g->nx * g->ny, nsg = (size_t)g->N * g->V * g->B;
+    void* fbuf = nullptr;
+    cudaError_t e = dev_alloc(&fbuf, sizeof(float) * nimg);
+    if (e != cudaSuccess) return cuda_fail(e, "autotune scratch");
+    float* f = (float*)fbuf;
+    const unsigned mask = g->prof_mask;
+    g->prof_mask = 0;
+    long long before[TNLM_KCLASS_COUNT];
+    for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) before[c] = g->launches[c];
+    // one outer iteration from the caller's start image fills the workspace
+    // (distances, minima, iterates) with the data the timed launches read
+    auto run = [&]() -> tnlm_status {
+        CK(cudaMemcpyAsync(f, d_f0, sizeof(float) * nimg, cudaMemcpyDeviceToDevice, st), "copy");
+        CK(cudaMemsetAsync(ws.st.iter, 0, sizeof(int), st), "reset");
+        LK(TNLM_KCLASS_PREP, launch_sqrt(d_winv, ws.sw, nsg, ws.st.err, st), "sqrt");
+        tnlm_status r = outer_iteration(g, p, d_y, f, st);
+        if (r != TNLM_OK) return r;
+        int best_g = 1, best_t = 1;
+        float tb = INFINITY;
+        for (int G = 1; G <= bp_max_groups(g); ++G) {
+            g->tune_bp_groups = G;
+            float ms = 0.f;
+            r = time_calls(st, 3, [&]() { return launch_backproject(g, ws.z, ws.gr, nullptr, ws.bps, st); }, &ms);
+            if (r != TNLM_OK) return r;
+            if (ms < tb) { tb = ms; best_g = G; }
+        }
+        if (p->m2 > 0) {
+            float tg = INFINITY;
+            for (int t = 1; t <= 3; ++t) {
+                g->tune_gj_tpb = t;
+                float ms = 0.f;
+                r = time_calls(st, 3, [&]() {
+                    return launch_gj_sweep(g, ws, p->window, p->h, p->mu_hat, ws.u, ws.U0, ws.U1, nullptr,
+                                           p->clamp, st);
+                }, &ms);
+                if (r != TNLM_OK) return r;
+                if (ms < tg) { tg = ms; best_t = t; }
+            }
+        }
+        g->tune_bp_groups = 0;
+        g->tune_gj_tpb = 0;
+        set_tuning(g, best_g, best_t);
+        CK(cudaMemsetAsync(ws.st.iter, 0, sizeof(int), st), "reset");
+        CK(cudaMemsetAsync(ws.st.err, 0, sizeof(int), st), "reset");
+        CK(cudaStreamSynchronize(st), "sync");
+        return TNLM_OK;
+    };
+    s = run();
+    g->prof_mask = mask;
+    for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) g->launches[c] = before[c];
+    cudaStreamSynchronize(st);
+    cudaFree(fbuf);
+    if (s != TNLM_OK) {
+        g->tune_bp_groups = 0;
+        g->tune_gj_tpb = 0;
+        return s;
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[key] = {g->tune_bp_groups, g->tune_gj_tpb};
+    return TNLM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched reconstruction: one outer iteration of every slice of the batch is
+// captured as a single CUDA graph -- one branch per slice, forked from and
+// joined to a capture stream -- and the graph is replayed once per outer
+// iteration, so kernels of different slices run side by side.  When slices
+// with fewer iterations finish, the graph is re-captured without them.
+// ---------------------------------------------------------------------------
+struct BatchItem {
+    unsigned long long uid;
+    unsigned tune_gen;
+    void* ws;
+    const float* y;
+    float* f;
+    tnlm_params p;
+    bool operator==(const BatchItem& o) const {
+        return uid == o.uid && tune_gen == o.tune_gen && ws == o.ws && y == o.y && f == o.f &&
+               same_shape(p, o.p);
+    }
+};
+
+struct BatchState {
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<BatchItem> key;
+    std::vector<std::array<long long, TNLM_KCLASS_COUNT>> launches;   // per slice and replay
+};
+std::mutex g_batch_mu;
+std::map<int, BatchState*> g_batch;   // per device
+
+tnlm_status batch_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
+                        const std::vector<const tnlm_params*>& ps, const std::vector<const float*>& ys,
+                        const std::vector<float*>& fs) {
+    std::vector<BatchItem> key(gs.size());
+    for (size_t j = 0; j < gs.size(); ++j)
+        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws.base, ys[j], fs[j], *ps[j]};
+    if (B->exec && key == B->key) return TNLM_OK;
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    if (!B->cap) CK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "capture stream");
+    while (B->streams.size() < gs.size()) {
+        cudaStream_t t;
+        CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "batch stream");
+        B->streams.push_back(t);
+    }
+    while (B->events.size() < gs.size() + 1) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
+        B->events.push_back(ev);
+    }
+    B->launches.assign(gs.size(), {});
+    CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    tnlm_status s = TNLM_OK;
+    cudaError_t e = cudaEventRecord(B->events[0], B->cap);
+    for (size_t j = 0; j < gs.size() && s == TNLM_OK && e == cudaSuccess; ++j) {
+        tnlm_geometry* g = gs[j];
+        e = cudaStreamWaitEvent(B->streams[j], B->events[0], 0);
+        if (e != cudaSuccess) break;
+        long long before[TNLM_KCLASS_COUNT];
+        for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) before[c] = g->launches[c];
+        const unsigned mask = g->prof_mask;
+        g->prof_mask = 0;
+        s = outer_iteration(g, ps[j], ys[j], fs[j], B->streams[j]);
+        g->prof_mask = mask;
+        for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) {
+            B->launches[j][c] = g->launches[c] - before[c];
+            g->launches[c] = before[c];
+        }
+        if (s != TNLM_OK) break;
+        e = cudaEventRecord(B->events[j + 1], B->streams[j]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cap, B->events[j + 1], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(B->cap, &graph);
+    if (s != TNLM_OK || e != cudaSuccess || ee != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (s != TNLM_OK) return s;
+        return cuda_fail(e != cudaSuccess ? e : ee, "batch capture");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&B->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        B->exec = nullptr;
+        return cuda_fail(ei, "batch graph instantiate");
+    }
+    B->key = key;
+    return TNLM_OK;
+}
+
+// Copies the monitors of the last reconstruction of g into rep and returns
+// the status its device flags call for (flags are cleared).
+tnlm_status read_report(tnlm_geometry* g, int done, tnlm_report* rep, cudaStream_t st) {
+    Workspace& ws = g->ws;
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, ws.st.err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
+    std::vector<double> hrel(done > 0 ? done : 1), hres(done > 0 ? done : 1);
+    if (done > 0) {
+        CK(cudaMemcpyAsync(hrel.data(), ws.st.hist_rel, sizeof(double) * done, cudaMemcpyDeviceToHost,
+                           st), "readback");
+        CK(cudaMemcpyAsync(hres.data(), ws.st.hist_res, sizeof(double) * done, cudaMemcpyDeviceToHost,
+                           st), "readback");
+    }
+    CK(cudaStreamSynchronize(st), "sync");
+    if (rep) {
+        rep->iterations = done;
+        rep->rel_change = done > 0 ? hrel[done - 1] : 0.0;
+        rep->data_residual = done > 0 ? hres[done - 1] : 0.0;
+        for (int k = 0; k < done; ++k) {
+            if (rep->rel_change_hist) rep->rel_change_hist[k] = hrel[k];
+            if (rep->residual_hist) rep->residual_hist[k] = hres[k];
+        }
+    }
+    if (err) {
+        CK(cudaMemsetAsync(ws.st.err, 0, sizeof(int), st), "reset");
+        if (err & 16)   // a bounded wait of the TMA sweep ran out
+            return fail(TNLM_ERR_TIMEOUT, "a device-side wait timed out (flags 0x%x)", err);
+        return fail(TNLM_ERR_NUMERIC, "non-finite value met on the device (flags 0x%x)", err);
+    }
     return TNLM_OK;
 }
 
@@ -409,6 +662,7 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
 
     tnlm_geometry* g = new tnlm_geometry();
+    g->uid = g_uid.fetch_add(1);
     g->device = d->device;
     g->nx = d->nx; g->ny = d->ny; g->N = d->n_phases; g->V = d->n_views; g->B = d->n_bins;
     g->pixel = d->pixel_mm; g->bin_mm = d->bin_mm; g->sid = d->sid_mm; g->sdd = d->sdd_mm;
@@ -483,7 +737,7 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
         return cuda_fail(e, "geometry table upload");
     }
     e = prepare_backproject(&g->cta_slots_bp);
-    if (e == cudaSuccess) e = prepare_weights();
+    if (e == cudaSuccess) e = prepare_weights(&g->cta_slots_gj);
     if (e != cudaSuccess) {
         tnlm_destroy_geometry(g);
         return cuda_fail(e, "kernel attributes");
@@ -713,34 +967,95 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* gc, const tnlm_params* p, cons
             if (rel < p->tol) break;
         }
     }
-    if (sync) {
-        int err = 0;
-        CK(cudaMemcpyAsync(&err, ws.st.err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
-        std::vector<double> hrel(done > 0 ? done : 1), hres(done > 0 ? done : 1);
-        if (done > 0) {
-            CK(cudaMemcpyAsync(hrel.data(), ws.st.hist_rel, sizeof(double) * done,
-                               cudaMemcpyDeviceToHost, st), "readback");
-            CK(cudaMemcpyAsync(hres.data(), ws.st.hist_res, sizeof(double) * done,
-                               cudaMemcpyDeviceToHost, st), "readback");
+    if (sync) return read_report(g, done, rep, st);
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y,
+                          const float* d_winv, const float* d_f0, int* bp_groups, int* gj_tiles,
+                          void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    tnlm_status s = check_params(p);
+    if (s != TNLM_OK) return s;
+    if (!d_y || !d_winv || !d_f0) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_y) || !aligned16(d_winv) || !aligned16(d_f0))
+        return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    s = autotune(g, p, d_y, d_winv, d_f0, (cudaStream_t)stream);
+    if (s != TNLM_OK) return s;
+    if (bp_groups) *bp_groups = g->tune_bp_groups;
+    if (gj_tiles) *gj_tiles = g->tune_gj_tpb;
+    return TNLM_OK;
+}
+
+tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_params* params,
+                                   int count, const float* const* d_y, const float* const* d_winv,
+                                   float* const* d_f, tnlm_report* reports, int autotune_shapes,
+                                   void* stream) {
+    g_err[0] = 0;
+    if (count < 1 || count > 4096) return fail(TNLM_ERR_INVALID_ARG, "count must be in [1, 4096]");
+    if (!geoms || !params || !d_y || !d_winv || !d_f) return fail(TNLM_ERR_INVALID_ARG, "NULL array");
+    int dev = -1, kmax = 0;
+    for (int i = 0; i < count; ++i) {
+        if (!geoms[i]) return fail(TNLM_ERR_INVALID_ARG, "geometry %d is NULL", i);
+        tnlm_status s = check_params(&params[i]);
+        if (s != TNLM_OK) return s;
+        if (params[i].tol != 0.0)
+            return fail(TNLM_ERR_INVALID_ARG, "batched slices run a fixed number of iterations (tol must be 0)");
+        if (!d_y[i] || !d_winv[i] || !d_f[i]) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer of slice %d", i);
+        if (!aligned16(d_y[i]) || !aligned16(d_winv[i]) || !aligned16(d_f[i]))
+            return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned (slice %d)", i);
+        if (dev < 0) dev = geoms[i]->device;
+        if (geoms[i]->device != dev) return fail(TNLM_ERR_INVALID_ARG, "all slices must be on one device");
+        for (int j = 0; j < i; ++j)
+            if (geoms[j] == geoms[i]) return fail(TNLM_ERR_INVALID_ARG, "slice %d repeats a handle", i);
+        kmax = params[i].k_outer > kmax ? params[i].k_outer : kmax;
+    }
+    DeviceGuard dg(dev);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int i = 0; i < count; ++i) {
+        tnlm_geometry* g = geoms[i];
+        const tnlm_params* p = &params[i];
+        if (autotune_shapes && g->tune_gen == 0) {
+            tnlm_status s = autotune(g, p, d_y[i], d_winv[i], d_f[i], st);
+            if (s != TNLM_OK) return s;
         }
-        CK(cudaStreamSynchronize(st), "sync");
-        if (rep) {
-            rep->iterations = done;
-            rep->rel_change = done > 0 ? hrel[done - 1] : 0.0;
-            rep->data_residual = done > 0 ? hres[done - 1] : 0.0;
-            for (int k = 0; k < done; ++k) {
-                if (rep->rel_change_hist) rep->rel_change_hist[k] = hrel[k];
-                if (rep->residual_hist) rep->residual_hist[k] = hres[k];
-            }
-        }
-        if (err) {
-            CK(cudaMemsetAsync(ws.st.err, 0, sizeof(int), st), "reset");
-            if (err & 16)   // a bounded wait of the TMA sweep ran out
-                return fail(TNLM_ERR_TIMEOUT, "a device-side wait timed out (flags 0x%x)", err);
-            return fail(TNLM_ERR_NUMERIC, "non-finite value met on the device (flags 0x%x)", err);
+        tnlm_status s = ensure_ws(g, (p->window - 1) / 2, p->k_outer < 1 ? 1 : p->k_outer, st);
+        if (s != TNLM_OK) return s;
+        const size_t nsg = (size_t)g->N * g->V * g->B;
+        CK(cudaMemsetAsync(g->ws.st.iter, 0, sizeof(int), st), "reset");
+        LK(TNLM_KCLASS_PREP, launch_sqrt(d_winv[i], g->ws.sw, nsg, g->ws.st.err, st), "sqrt");
+    }
+    {
+        std::lock_guard<std::mutex> lock(g_batch_mu);
+        BatchState*& B = g_batch[dev];
+        if (!B) B = new BatchState();
+        std::vector<tnlm_geometry*> gs;
+        std::vector<const tnlm_params*> ps;
+        std::vector<const float*> ys;
+        std::vector<float*> fs;
+        for (int k = 0; k < kmax; ++k) {
+            gs.clear(); ps.clear(); ys.clear(); fs.clear();
+            for (int i = 0; i < count; ++i)
+                if (k < params[i].k_outer) {
+                    gs.push_back(geoms[i]); ps.push_back(&params[i]); ys.push_back(d_y[i]); fs.push_back(d_f[i]);
+                }
+            tnlm_status s = batch_graph(B, gs, ps, ys, fs);
+            if (s != TNLM_OK) return s;
+            CK(cudaGraphLaunch(B->exec, st), "batch graph launch");
+            for (size_t j = 0; j < gs.size(); ++j)
+                for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) gs[j]->launches[c] += B->launches[j][c];
         }
     }
-    return TNLM_OK;
+    tnlm_status first = TNLM_OK;
+    for (int i = 0; i < count; ++i) {
+        tnlm_status s = read_report(geoms[i], params[i].k_outer, reports ? &reports[i] : nullptr, st);
+        if (s != TNLM_OK && first == TNLM_OK) first = s;
+    }
+    return first;
 }
 
 }  // extern "C"

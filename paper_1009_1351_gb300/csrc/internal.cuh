@@ -74,11 +74,11 @@ struct Workspace {
     DevState st{};
     // TMA descriptors of the distance planes [N*W2max][py][px]: boxes of
     // 64 x 16 (forward rows) and 68 x 16 (backward rows) floats
-    alignas(64) CUtensorMap tmF{};
-    alignas(64) CUtensorMap tmB{};
+    CUtensorMap tmF{};
+    CUtensorMap tmB{};
     // and of the Gauss-Jacobi iterates U0 / U1 [N][py][px]: box 80 x 30
-    alignas(64) CUtensorMap tmU0{};
-    alignas(64) CUtensorMap tmU1{};
+    CUtensorMap tmU0{};
+    CUtensorMap tmU1{};
     bool tm_ok = false;
 };
 
@@ -94,6 +94,13 @@ struct tnlm_geometry {
     float* d_fbp_taps = nullptr; // [2B-1] discrete equiangular ramp kernel of the initial FBP
     tnlm::Workspace ws;
     int cta_slots_bp = 0;       // resident backprojector CTAs on the device
+    int cta_slots_gj = 0;       // resident TMA-sweep CTAs on the device
+    // launch choices set by tnlm_autotune (0 = built-in heuristic); tune_gen
+    // changes whenever they do, so captured graphs are re-captured
+    int tune_bp_groups = 0;     // view groups (CTAs) per backprojection tile
+    int tune_gj_tpb = 0;        // tiles per CTA of the TMA sweep
+    unsigned tune_gen = 0;
+    unsigned long long uid = 0; // unique per handle (graph and batch keys)
     // CUDA graph of one outer iteration (see api.cu)
     void* graph = nullptr;
     // profiling: launch counters and event-bracketed timing (see api.cu)
@@ -120,8 +127,9 @@ cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R,
 cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
                            const ProjOut& o, cudaStream_t st);
 cudaError_t prepare_backproject(int* slots);
-cudaError_t prepare_weights();
+cudaError_t prepare_weights(int* gj_slots);   // also counts resident TMA-sweep CTAs
 int bp_blocks_per_phase(const tnlm_geometry* g);
+int bp_max_groups(const tnlm_geometry* g);      // largest useful view-group count
 size_t static_scratch_floats();
 cudaError_t static_scratch_ptr(float** out);
 size_t bp_scratch_floats(const tnlm_geometry* g);

@@ -449,7 +449,13 @@ cudaError_t prepare_backproject(int* slots) {
     return cudaSuccess;
 }
 
+int bp_max_groups(const tnlm_geometry* g) {
+    const int m = (g->V + kBpWarps - 1) / kBpWarps;
+    return m < kBpMaxGroups ? m : kBpMaxGroups;
+}
+
 static int bp_groups(const tnlm_geometry* g) {
+    if (g->tune_bp_groups > 0) return min(g->tune_bp_groups, bp_max_groups(g));
     const int slots = g->cta_slots_bp > 0 ? g->cta_slots_bp : 1;
     const int tiles = bp_blocks_per_phase(g) * g->N;
     int best = 1;

@@ -11,10 +11,15 @@
 // for both directions:
 //   m_next_i(x)     = min_s D_i(x, s)            (row x of phase i toward i+1)
 //   m_prev_{i+1}(y) = min_s D_i(y - s, s)        (row y of phase i+1 toward i)
-// A block owns a 32 x 16 tile T of one pair.  For each shift it forms the
-// horizontal patch sums over the bounding box of T and T - s (staged in
-// shared memory), then each thread sums them vertically for its own pixel
-// (forward row) and for the pixel it receives from (backward row).
+// A block owns a 64 x TY tile T of one pair (TY = 32 - 2r rounded down to a
+// multiple of 4).  For each shift, pass 1 forms 32 rows of horizontal patch
+// sums (8 adjacent sums per thread from a register window of squared
+// differences) into one of two shared buffers while pass 2 sums the other
+// buffer vertically (one column, TY/4 rows per thread), stores the forward
+// distances, keeps the forward row minima in registers and folds each
+// distance into a shared array of backward minima at x + s; one barrier per
+// shift.  The backward minima of T's rho-neighbourhood are combined across
+// blocks with an integer atomic min at the end.
 //
 // K5 (k_gj) is one Gauss-Jacobi sweep, one thread per pixel of one phase.  It
 // streams the two distance planes that touch phase i (pair i forward at x,
@@ -40,163 +45,225 @@ struct WArgs {
     int nx, ny, N, rho, W;
 };
 
-// Shared-memory geometry of k_weights for window radius rho, patch radius R.
-struct WSmem {
-    int GW, GH;   // g tiles (with a spare float4 of columns)
-    int HP, HH;   // horizontal sums: pitch, rows
-    int DR;       // rows of one distance box
-    __host__ __device__ WSmem(int rho, int R) {
-        // odd pitch: lanes on consecutive rows hit distinct banks
-        GW = (kWTileX + 2 * (rho + R) + 4) | 1;
-        GH = kWTileY + 2 * (rho + R);
-        // pitch/4 odd: float4 stores of consecutive rows hit distinct bank groups
-        HP = ((kWTileX + rho + 4) + 3) / 4 * 4;
-        if (((HP / 4) & 1) == 0) HP += 4;
-        HH = kWTileY + rho + 2 * R + 4;
-        DR = kWTileY + rho + 4;
+// Shared-memory geometry of k_weights.  The output tile is 64 columns by
+// TY rows, TY = 4 floor((32 - 2R) / 4), so that the TY + 2R rows of
+// horizontal sums fit one 32-row pass.
+template <int R>
+struct WGeo {
+    static constexpr int TX = 64;
+    static constexpr int TY = (32 - 2 * R) / 4 * 4;
+    static constexpr int HR = TY + 2 * R;       // rows of horizontal sums (<= 32)
+    static constexpr int RPT = TY / 4;          // output rows per thread
+    static constexpr int NQ = 8 + 2 * R;        // taps of 8 adjacent horizontal sums
+    static constexpr int NQ4 = (NQ + 3) / 4;    // float4 loads of a g_i row segment
+    // g_i tile: TY + 2R rows, pitch a multiple of 4 with pitch/4 odd (float4
+    // loads of two consecutive rows fall in distinct bank groups)
+    static constexpr int GIW0 = (TX + 2 * R + 3) / 4 * 4;
+    static constexpr int GIW = ((GIW0 / 4) & 1) ? GIW0 : GIW0 + 4;
+    static constexpr int GIH = TY + 2 * R;
+    static constexpr int HP = 68;               // horizontal-sum pitch (68 / 4 odd)
+    static constexpr int BMW = TX + 2 * ((kMaxWindow - 1) / 2);   // backward-minimum pitch
+    int GJW, GJH, GJS, BMH;
+    __host__ __device__ explicit WGeo(int rho) {
+        GJW = (TX + 2 * rho + 2 * R) | 1;       // odd: rows of a warp hit distinct banks
+        GJH = TY + 2 * rho + 2 * R;
+        GJS = (GJW * GJH + 3) / 4 * 4;          // keeps the next buffer 16-byte aligned
+        BMH = TY + 2 * rho;
     }
     __host__ __device__ size_t floats() const {
-        return 2 * (size_t)GW * GH + (size_t)HP * HH + 2 * (size_t)HP * DR;
+        return (size_t)GIW * GIH + (size_t)GJS + 2 * 32 * (size_t)HP + (size_t)BMW * BMH;
     }
 };
 
 template <int R>
-__global__ void __launch_bounds__(256) k_weights(WArgs a) {
-    extern __shared__ float sm[];
+__global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
+    using G = WGeo<R>;
+    extern __shared__ __align__(16) float sm[];
     const int rho = a.rho, W = a.W;
-    const WSmem L(rho, R);
-    float* Gi = sm;
-    float* Gj = Gi + L.GW * L.GH;
-    float* H = Gj + L.GW * L.GH;
-    float* Db = H + L.HP * L.HH;              // two distance boxes
-    const int p = blockIdx.z, j = (p + 1) % a.N;
-    const int X0 = blockIdx.x * kWTileX, Y0 = blockIdx.y * kWTileY;
-    const int gx0 = X0 - rho - R, gy0 = Y0 - rho - R;
-    const int tid = threadIdx.x;
+    const G L(rho);
+    float* Gi = sm;                                  // g_p at rows Y0-R.., columns X0-R..
+    float* Gj = Gi + G::GIW * G::GIH;                // g_q at rows Y0-rho-R.., columns X0-rho-R..
+    float* H = Gj + L.GJS;                           // two buffers of 32 x HP
+    float* BM = H + 2 * 32 * G::HP;                  // backward minima at rows Y0-rho.., columns X0-rho..
+    const int p = blockIdx.z, q = (p + 1) % a.N;
+    const int X0 = blockIdx.x * G::TX, Y0 = blockIdx.y * G::TY;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nx = a.nx, ny = a.ny;
     const size_t npx = (size_t)nx * ny;
     const float* gp = a.g + p * npx;
-    const float* gq = a.g + j * npx;
-    for (int e = tid; e < L.GW * L.GH; e += 256) {
-        const int x = gx0 + e % L.GW, y = gy0 + e / L.GW;
-        const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
-        Gi[e] = in ? gp[(size_t)y * nx + x] : 0.f;
-        Gj[e] = in ? gq[(size_t)y * nx + x] : 0.f;
-    }
-    for (int e = tid; e < L.HP * L.HH; e += 256) H[e] = 0.f;
-    const int tx = tid & 31, ty = tid >> 5;
-    if (a.U0) {  // padded copy of g_p: u^(0) of the Gauss-Jacobi sweeps
-        for (int kk = 0; kk < 2; ++kk) {
-            const int x = X0 + tx, y = Y0 + ty + 8 * kk;
-            if (x < nx && y < ny)
-                a.U0[p * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] =
-                    gp[(size_t)y * nx + x];
+    const float* gq = a.g + q * npx;
+    for (int r = warp; r < G::GIH; r += 8)
+        for (int c = lane; c < G::GIW; c += 32) {
+            const int x = X0 - R + c, y = Y0 - R + r;
+            Gi[r * G::GIW + c] = (x >= 0 && x < nx && y >= 0 && y < ny) ? gp[(size_t)y * nx + x] : 0.f;
         }
-    }
+    for (int r = warp; r < L.GJH; r += 8)
+        for (int c = lane; c < L.GJW; c += 32) {
+            const int x = X0 - rho - R + c, y = Y0 - rho - R + r;
+            Gj[r * L.GJW + c] = (x >= 0 && x < nx && y >= 0 && y < ny) ? gq[(size_t)y * nx + x] : 0.f;
+        }
+    for (int e = tid; e < G::BMW * L.BMH; e += 256) BM[e] = INFINITY;
     __syncthreads();
+    if (a.U0) {  // padded copy of g_p: u^(0) of the Gauss-Jacobi sweeps
+        for (int r = warp; r < G::TY; r += 8)
+            for (int c = lane; c < G::TX; c += 32) {
+                const int x = X0 + c, y = Y0 + r;
+                if (x < nx && y < ny)
+                    a.U0[p * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] =
+                        Gi[(r + R) * G::GIW + c + R];
+            }
+    }
 
-    float mf[2] = {INFINITY, INFINITY}, mb[2] = {INFINITY, INFINITY};
-    const size_t W2 = (size_t)W * W;
-    float* Dp = a.D + (size_t)p * W2 * a.pp.plane;
-    for (int sy = -rho; sy <= rho; ++sy) {
-        for (int sx = -rho; sx <= rho; ++sx) {
-            const int k = (sy + rho) * W + (sx + rho);
-            float* D = Db + (k & 1) * L.HP * L.DR;
-            // box = bounding box of the tile and of the tile shifted by -s
-            const int bw = kWTileX + abs(sx), bh = kWTileY + abs(sy);
-            const int ox = X0 + min(0, -sx), oy = Y0 + min(0, -sy);
-            // (1) horizontal patch sums, 4 adjacent box columns per task, on
-            //     box rows widened by r: H(c, r') = sum_q d2(c + q, r' - R)
-            const int ncg = (bw + 3) / 4, nrow = bh + 2 * R;
-            for (int e = tid; e < ncg * nrow; e += 256) {
-                const int cr = e % nrow, cg = e / nrow;     // rows fastest: conflict-free
-                const int zx = ox + 4 * cg - R, zy = oy + cr - R;   // leftmost tap
-                const float* pi = Gi + (zy - gy0) * L.GW + (zx - gx0);
-                const float* pj = Gj + (zy + sy - gy0) * L.GW + (zx + sx - gx0);
-                float d2[4 + 2 * R];
+    // pass-1 task: H row hr, 8 adjacent columns from 8 g
+    const int g8 = 8 * ((warp & 1) * 4 + (lane & 3));
+    const int hr = (warp >> 1) * 8 + (lane >> 2);
+    // pass-2 task: output column c2, output rows r2 .. r2 + RPT - 1
+    const int c2 = (warp & 1) * 32 + lane;
+    const int r2 = (warp >> 1) * G::RPT;
+    const int x2 = X0 + c2;
+    const bool xin = x2 < nx;
+
+    // (1) horizontal patch sums of shift (sx, sy) into buffer b:
+    //     H(hr, c) = sum_{t=0..2R} d2(c + t - R, hr - R),  d2 = (g_p(x) - g_q(x + s))^2
+    auto horizontal = [&](int sx, int sy, float* Hb) {
+        if (hr >= G::HR) return;
+        float d2[4 * G::NQ4];
+        const float* pi = Gi + hr * G::GIW + g8;
+        const float* pj = Gj + (hr + sy + rho) * L.GJW + g8 + sx + rho;
 #pragma unroll
-                for (int q = 0; q < 4 + 2 * R; ++q) {
-                    const float d = pi[q] - pj[q];
-                    d2[q] = d * d;
+        for (int t = 0; t < G::NQ4; ++t) {
+            const float4 v = *(const float4*)(pi + 4 * t);
+            const float vi[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (4 * t + u < G::NQ) {
+                    const float d = vi[u] - pj[4 * t + u];
+                    d2[4 * t + u] = d * d;
                 }
-                float h[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    float t = 0.f;
-#pragma unroll
-                    for (int q = 0; q <= 2 * R; ++q) t += d2[c + q];
-                    h[c] = t;
-                }
-                *(float4*)(H + cr * L.HP + 4 * cg) = make_float4(h[0], h[1], h[2], h[3]);
-            }
-            __syncthreads();
-            // (2) vertical sums, 4 adjacent box rows per task: D(c, r) = sum_q H(c, r + q)
-            const int nrg = (bh + 3) / 4;
-            for (int e = tid; e < bw * nrg; e += 256) {
-                const int c = e % bw, rg = e / bw;
-                float hv[4 + 2 * R];
-#pragma unroll
-                for (int q = 0; q < 4 + 2 * R; ++q) hv[q] = H[(4 * rg + q) * L.HP + c];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    float t = 0.f;
-#pragma unroll
-                    for (int q = 0; q <= 2 * R; ++q) t += hv[r + q];
-                    D[(4 * rg + r) * L.HP + c] = t;
-                }
-            }
-            __syncthreads();
-            // (3) forward distance (stored) and backward row minimum of this thread's pixels
-#pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-                const int x = X0 + tx, y = Y0 + ty + 8 * kk;
-                const bool in = x < nx && y < ny;
-                const float df = D[(y - oy) * L.HP + (x - ox)];
-                const bool vf = in && x + sx >= 0 && x + sx < nx && y + sy >= 0 && y + sy < ny;
-                if (in)
-                    Dp[(size_t)k * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] =
-                        vf ? df : INFINITY;
-                if (vf) mf[kk] = fminf(mf[kk], df);
-                const float db = D[(y - sy - oy) * L.HP + (x - sx - ox)];
-                const bool vb = in && x - sx >= 0 && x - sx < nx && y - sy >= 0 && y - sy < ny;
-                if (vb) mb[kk] = fminf(mb[kk], db);
             }
         }
-    }
+        float h[8];
 #pragma unroll
-    for (int kk = 0; kk < 2; ++kk) {
-        const int x = X0 + tx, y = Y0 + ty + 8 * kk;
-        if (x < nx && y < ny) {
-            const size_t pix = (size_t)y * nx + x;
-            a.mins[p * npx + pix] = mf[kk];                        // m_next of phase p
-            a.mins[(size_t)(a.N + j) * npx + pix] = mb[kk];        // m_prev of phase p+1
-            if (!(mf[kk] < INFINITY) || !(mb[kk] < INFINITY)) atomicOr(a.err, 4);
+        for (int c = 0; c < 8; c += 2) {
+            float m = 0.f;
+#pragma unroll
+            for (int t = 1; t <= 2 * R; ++t) m = (t == 1) ? d2[c + 1] : m + d2[c + t];
+            h[c] = (R == 0) ? d2[c] : d2[c] + m;
+            h[c + 1] = (R == 0) ? d2[c + 1] : m + d2[c + 2 * R + 1];
+        }
+        float* o = Hb + hr * G::HP + g8;
+        *(float4*)o = make_float4(h[0], h[1], h[2], h[3]);
+        *(float4*)(o + 4) = make_float4(h[4], h[5], h[6], h[7]);
+    };
+
+    float mf[G::RPT];
+#pragma unroll
+    for (int r = 0; r < G::RPT; ++r) mf[r] = INFINITY;
+    const size_t plane = a.pp.plane;
+    float* Dbase = a.D + (size_t)p * W * W * plane + (size_t)(Y0 + r2 + a.pp.oy) * a.pp.px + x2 + a.pp.ox;
+
+    horizontal(-rho, -rho, H);
+    __syncthreads();
+    const int W2 = W * W;
+    int sx = -rho, sy = -rho;
+    for (int k = 0; k < W2; ++k) {
+        if (k + 1 < W2) {
+            const int nx1 = (sx == rho) ? -rho : sx + 1;
+            const int ny1 = (sx == rho) ? sy + 1 : sy;
+            horizontal(nx1, ny1, H + ((k + 1) & 1) * 32 * G::HP);
+        }
+        // (2) vertical sums: D(c2, r) = sum_{t=0..2R} H(r + t, c2)
+        {
+            const float* Hb = H + (k & 1) * 32 * G::HP + r2 * G::HP + c2;
+            float hv[G::RPT + 2 * R];
+#pragma unroll
+            for (int t = 0; t < G::RPT + 2 * R; ++t) hv[t] = Hb[t * G::HP];
+            float dv[G::RPT];
+#pragma unroll
+            for (int r = 0; r < G::RPT; r += 2) {
+                float m = 0.f;
+#pragma unroll
+                for (int t = 1; t <= 2 * R; ++t) m = (t == 1) ? hv[r + 1] : m + hv[r + t];
+                dv[r] = (R == 0) ? hv[r] : hv[r] + m;
+                if (r + 1 < G::RPT) dv[r + 1] = (R == 0) ? hv[r + 1] : m + hv[r + 2 * R + 1];
+            }
+            // (3) store the forward distance (+inf where x + s leaves the image),
+            //     track the forward row minimum and the backward minimum at x + s
+            const bool colok = xin && (unsigned)(x2 + sx) < (unsigned)nx;
+            float* Dk = Dbase + (size_t)k * plane;
+            float* bm = BM + (r2 + sy + rho) * G::BMW + c2 + sx + rho;
+            const int y0 = Y0 + r2;
+            if (y0 + G::RPT <= ny && y0 + sy >= 0 && y0 + G::RPT - 1 + sy < ny) {
+                // every row of this warp and its shifted row lie in the image
+#pragma unroll
+                for (int r = 0; r < G::RPT; ++r) {
+                    const float val = colok ? dv[r] : INFINITY;
+                    if (xin) Dk[(size_t)r * a.pp.px] = val;
+                    mf[r] = fminf(mf[r], val);
+                    bm[r * G::BMW] = fminf(bm[r * G::BMW], val);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < G::RPT; ++r) {
+                    const int y = y0 + r;
+                    const bool yin = y < ny;
+                    const bool vf = colok && yin && (unsigned)(y + sy) < (unsigned)ny;
+                    const float val = vf ? dv[r] : INFINITY;
+                    if (xin && yin) Dk[(size_t)r * a.pp.px] = val;
+                    mf[r] = fminf(mf[r], val);
+                    bm[r * G::BMW] = fminf(bm[r * G::BMW], val);
+                }
+            }
+        }
+        __syncthreads();
+        if (sx == rho) { sx = -rho; ++sy; } else { ++sx; }
+    }
+    // forward minima: owned by this thread
+#pragma unroll
+    for (int r = 0; r < G::RPT; ++r) {
+        const int y = Y0 + r2 + r;
+        if (xin && y < ny) {
+            a.mins[p * npx + (size_t)y * nx + x2] = mf[r];
+            if (!(mf[r] < INFINITY)) atomicOr(a.err, 4);
         }
     }
+    // backward minima of phase q toward p: a pixel receives from every block
+    // whose tile lies within rho of it; combine with an integer atomic min
+    // (the order of non-negative floats is that of their bit patterns)
+    int* mprev = (int*)(a.mins + (size_t)(a.N + q) * npx);
+    for (int r = warp; r < L.BMH; r += 8)
+        for (int c = lane; c < G::TX + 2 * rho; c += 32) {
+            const int x = X0 - rho + c, y = Y0 - rho + r;
+            const float v = BM[r * G::BMW + c];
+            if (x >= 0 && x < nx && y >= 0 && y < ny && v < INFINITY)
+                atomicMin(mprev + (size_t)y * nx + x, __float_as_int(v));
+        }
 }
 
-static size_t weights_smem(int rho, int R) { return sizeof(float) * WSmem(rho, R).floats(); }
+template <int R>
+static size_t weights_smem(int rho) { return sizeof(float) * WGeo<R>(rho).floats(); }
 
-static cudaError_t prepare_gj_tma();
+static cudaError_t prepare_gj_tma(int* slots);
 
 // Opt every weight-kernel variant into the largest dynamic shared memory any
 // window can need (called at geometry creation, outside any stream capture).
-cudaError_t prepare_weights() {
+cudaError_t prepare_weights(int* gj_slots) {
     cudaError_t e = cudaSuccess;
 #define TNLM_PREP_W(R)                                                                  \
     if (e == cudaSuccess)                                                               \
         e = cudaFuncSetAttribute(k_weights<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)weights_smem((kMaxWindow - 1) / 2, R));
+                                 (int)weights_smem<R>((kMaxWindow - 1) / 2));
     TNLM_PREP_W(0) TNLM_PREP_W(1) TNLM_PREP_W(2) TNLM_PREP_W(3)
     TNLM_PREP_W(4) TNLM_PREP_W(5) TNLM_PREP_W(6) TNLM_PREP_W(7)
 #undef TNLM_PREP_W
-    return e == cudaSuccess ? prepare_gj_tma() : e;
+    return e == cudaSuccess ? prepare_gj_tma(gj_slots) : e;
 }
 
 template <int R>
 static cudaError_t launch_weights_r(const WArgs& a, cudaStream_t st) {
-    const size_t smem = weights_smem(a.rho, R);
-    dim3 grid((a.nx + kWTileX - 1) / kWTileX, (a.ny + kWTileY - 1) / kWTileY, a.N);
+    using G = WGeo<R>;
+    const size_t smem = weights_smem<R>(a.rho);
+    dim3 grid((a.nx + G::TX - 1) / G::TX, (a.ny + G::TY - 1) / G::TY, a.N);
     k_weights<R><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -206,6 +273,10 @@ cudaError_t launch_weights(const tnlm_geometry* g, const Workspace& ws, int patc
     WArgs a;
     a.g = gimg; a.D = ws.D; a.mins = ws.mins; a.U0 = ws.U0; a.err = ws.st.err; a.pp = ws.pp;
     a.nx = g->nx; a.ny = g->ny; a.N = g->N; a.rho = (window - 1) / 2; a.W = window;
+    // backward minima start above every distance (0x7f7f7f7f = 3.4e38)
+    const size_t npx = (size_t)g->nx * g->ny;
+    cudaError_t e = cudaMemsetAsync(ws.mins + (size_t)g->N * npx, 0x7f, sizeof(float) * g->N * npx, st);
+    if (e != cudaSuccess) return e;
     switch ((patch - 1) / 2) {
         case 0: return launch_weights_r<0>(a, st);
         case 1: return launch_weights_r<1>(a, st);
@@ -450,7 +521,7 @@ constexpr int kTmaBW = kTmaTW + 4;
 constexpr int kTmaConsumers = 256;
 constexpr int kTmaThreads = kTmaConsumers + 32;
 constexpr int kTmaStageFloats = kTmaTH * (kTmaTW + kTmaBW);   // 2112 floats = 66 x 128 B
-constexpr int kTmaStages = 6;
+constexpr int kTmaStages = 4;
 constexpr long kTmaSpinLimit = 1L << 24;
 // neighbour-phase tile: the 64 x 16 pixels widened by 8 columns and 7 rows
 // on each side (every window up to 15 x 15), loaded once per block
@@ -461,6 +532,9 @@ struct TmaMaps {
     CUtensorMap F, B, U;     // forward / backward distance boxes, iterate tile box
 };
 
+__device__ __forceinline__ float f4get(const float4& v, int c) {
+    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
     return (unsigned)__cvta_generic_to_shared(p);
 }
@@ -500,28 +574,32 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
 }
 
 template <int W, int MODE>
-__global__ void __launch_bounds__(kTmaThreads) k_gj_tma(GjArgs a, const __grid_constant__ CUtensorMap tmF,
+__global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __grid_constant__ CUtensorMap tmF,
                                                         const __grid_constant__ CUtensorMap tmB,
-                                                        const __grid_constant__ CUtensorMap tmU) {
+                                                        const __grid_constant__ CUtensorMap tmU,
+                                                        int tpb) {
     constexpr int RHO = (W - 1) / 2;
     constexpr int UOFF = 4 * ((RHO + 3) / 4);
-    constexpr int UW = 4 + 2 * UOFF;
+    constexpr int NCH = (2 * UOFF + 4) / 4;     // float4 chunks of a window row
     constexpr int NK = W * W;
     extern __shared__ __align__(128) float tma_sm_raw[];
     // tensor-copy destinations must be 128-byte aligned: round the base up
     float* stages = (float*)(((uintptr_t)tma_sm_raw + 127) & ~(uintptr_t)127);
-    float* utile = stages + kTmaStages * kTmaStageFloats;          // [2][kTmaUH][kTmaUW]
-    uint64_t* full = (uint64_t*)(utile + 2 * kTmaUFloats);
+    float* utile = stages + kTmaStages * kTmaStageFloats;     // [2 buffers][2 phases][UH][UW]
+    uint64_t* full = (uint64_t*)(utile + 4 * kTmaUFloats);
     uint64_t* empty = full + kTmaStages;
-    uint64_t* ubar = empty + kTmaStages;
-    __shared__ int s_abort, s_issued;
+    uint64_t* ufull = empty + kTmaStages;                      // [2]
+    uint64_t* uempty = ufull + 2;                              // [2]
+    __shared__ int s_abort, s_issued, s_uissued;
     __shared__ double wsum[2][kTmaConsumers / 32];
     const int N = a.N, nx = a.nx, ny = a.ny;
-    const int tile = blockIdx.x / N, i = blockIdx.x % N;
     const int tilesx = (nx + kTmaTW - 1) / kTmaTW;
+    const int ntiles = tilesx * ((ny + kTmaTH - 1) / kTmaTH) * N;
+    // tiles blockIdx.x, + gridDim.x, ...: the tiles in flight at any moment
+    // stay a contiguous run of the tile-major, phase-minor order, so the
+    // second read of each distance plane is served by L2
+    const int t0 = blockIdx.x, tstep = gridDim.x, t1 = min(ntiles, t0 + tpb * tstep);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int X0 = (tile % tilesx) * kTmaTW, Y0 = (tile / tilesx) * kTmaTH;
-    const int ip = (i + N - 1) % N, inx = (i + 1) % N;
     const int px = a.pp.px;
     const size_t plane = a.pp.plane;
     if (tid == 0) {
@@ -529,106 +607,147 @@ __global__ void __launch_bounds__(kTmaThreads) k_gj_tma(GjArgs a, const __grid_c
             mbar_init(&full[st], 1);
             mbar_init(&empty[st], kTmaConsumers / 32);
         }
-        mbar_init(ubar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ufull[b], 1);
+            mbar_init(&uempty[b], kTmaConsumers / 32);
+        }
         s_abort = 0;
         s_issued = 0;
+        s_uissued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     if (warp == kTmaConsumers / 32) {
-        if (lane == 0) {   // producer
-            // the two neighbour-phase tiles (rows/columns outside the plane read 0)
-            mbar_arrive_expect_tx(ubar, 8u * kTmaUFloats);
-            tma_load_3d(utile, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, inx, ubar);
-            tma_load_3d(utile + kTmaUFloats, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, ip, ubar);
-            int k = 0;
-            for (; k < NK; ++k) {
-                const int slot = k % kTmaStages;
-                if (k >= kTmaStages &&
-                    !mbar_wait_bounded(&empty[slot], (unsigned)((k / kTmaStages - 1) & 1))) {
-                    s_abort = 1;
-                    break;
-                }
-                if (*(volatile int*)&s_abort) break;
-                const int dy = k / W - RHO, dx = k % W - RHO;
-                const int off = -dx;
-                const int base = off >= 0 ? (off / 4) * 4 : -(((-off) + 3) / 4) * 4;
-                float* stg = stages + slot * kTmaStageFloats;
-                mbar_arrive_expect_tx(&full[slot], 4u * kTmaStageFloats);
-                tma_load_3d(stg, &tmF, X0 + a.pp.ox, Y0 + a.pp.oy, i * NK + k, &full[slot]);
-                tma_load_3d(stg + kTmaTH * kTmaTW, &tmB, X0 + a.pp.ox + base, Y0 + a.pp.oy - dy,
-                            ip * NK + k, &full[slot]);
-            }
-            s_issued = k;
-        }
-    } else {
-        const int tx = tid % 16, ty = tid / 16;
-        const int x0 = X0 + 4 * tx, y = Y0 + ty;
-        const bool rowin = x0 < nx && y < ny;
-        const size_t npx = (size_t)nx * ny;
-        float af[4] = {0.f, 0.f, 0.f, 0.f}, zf[4] = {0.f, 0.f, 0.f, 0.f};
-        float ab[4] = {0.f, 0.f, 0.f, 0.f}, zb[4] = {0.f, 0.f, 0.f, 0.f};
-        const float k2 = a.k2;
-        float mfk[4], mbk[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const bool in = rowin && x0 + p < nx;
-            const size_t pix = (size_t)y * nx + x0 + p;
-            mfk[p] = in ? a.mins[i * npx + pix] * k2 : 0.f;
-            mbk[p] = in ? a.mins[(N + i) * npx + pix] * k2 : 0.f;
-        }
-        // window rows of this thread inside the neighbour tiles
-        const float* Un = utile + (ty + 7) * kTmaUW + 4 * tx + 8 - UOFF;
-        const float* Up = utile + kTmaUFloats + (ty + 7) * kTmaUW + 4 * tx + 8 - UOFF;
-        bool ok = mbar_wait_bounded(ubar, 0u);
-        if (!ok) s_abort = 1;
-        int k = 0;
-        for (int sy = 0; sy < W && ok; ++sy) {
-            const int dy = sy - RHO;
-            float un[UW], up[UW];
-#pragma unroll
-            for (int q = 0; q < UW / 4; ++q) {
-                const float4 vn = *((const float4*)(Un + dy * kTmaUW) + q);
-                const float4 vp = *((const float4*)(Up - dy * kTmaUW) + q);
-                un[4 * q] = vn.x; un[4 * q + 1] = vn.y; un[4 * q + 2] = vn.z; un[4 * q + 3] = vn.w;
-                up[4 * q] = vp.x; up[4 * q + 1] = vp.y; up[4 * q + 2] = vp.z; up[4 * q + 3] = vp.w;
-            }
-#pragma unroll
-            for (int sx = 0; sx < W; ++sx, ++k) {
-                const int dx = sx - RHO;
-                const int slot = k % kTmaStages;
-                if (!mbar_wait_bounded(&full[slot], (unsigned)((k / kTmaStages) & 1))) {
-                    s_abort = 1;
+        if (lane == 0) {   // producer: runs ahead across the block's tiles
+            int kk = 0, nu = 0;
+            bool ok = true;
+            for (int t = t0, u = 0; t < t1 && ok; t += tstep, ++u) {
+                const int ub = u & 1;
+                const int tile = t / N, i = t % N;
+                const int X0 = (tile % tilesx) * kTmaTW, Y0 = (tile / tilesx) * kTmaTH;
+                const int ip = (i + N - 1) % N, inx = (i + 1) % N;
+                // iterate tiles of both neighbour phases (rows/columns outside the plane read 0)
+                if (u >= 2 && !mbar_wait_bounded(&uempty[ub], (unsigned)(((u - 2) >> 1) & 1))) {
                     ok = false;
                     break;
                 }
-                const float* stg = stages + slot * kTmaStageFloats;
-                const float4 f4 = *(const float4*)(stg + ty * kTmaTW + 4 * tx);
-                const int off = -dx;
-                const int base = off >= 0 ? (off / 4) * 4 : -(((-off) + 3) / 4) * 4;
-                const int sh = off - base;
-                const float* pb = stg + kTmaTH * kTmaTW + ty * kTmaBW + 4 * tx;
-                const float4 b0 = *(const float4*)pb;
-                const float4 b1 = *(const float4*)(pb + 4);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the stage
-                const float df[4] = {f4.x, f4.y, f4.z, f4.w};
-                const float w8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-                for (int p = 0; p < 4; ++p) {
-                    const float ef = ex2_approx(fmaf(-df[p], k2, mfk[p]));
-                    const float eb = ex2_approx(fmaf(-w8[sh + p], k2, mbk[p]));
-                    af[p] = fmaf(ef, un[UOFF + p + dx], af[p]);
-                    ab[p] = fmaf(eb, up[UOFF + p - dx], ab[p]);
-                    zf[p] += ef;
-                    zb[p] += eb;
+                float* ut = utile + ub * 2 * kTmaUFloats;
+                mbar_arrive_expect_tx(&ufull[ub], 8u * kTmaUFloats);
+                tma_load_3d(ut, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, inx, &ufull[ub]);
+                tma_load_3d(ut + kTmaUFloats, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, ip, &ufull[ub]);
+                nu = u + 1;
+                for (int k = 0; k < NK; ++k) {
+                    const int slot = kk % kTmaStages;
+                    if (kk >= kTmaStages &&
+                        !mbar_wait_bounded(&empty[slot], (unsigned)((kk / kTmaStages - 1) & 1))) {
+                        ok = false;
+                        break;
+                    }
+                    if (*(volatile int*)&s_abort) {
+                        ok = false;
+                        break;
+                    }
+                    const int dy = k / W - RHO, dx = k % W - RHO;
+                    const int off = -dx;
+                    const int base = off >= 0 ? (off / 4) * 4 : -(((-off) + 3) / 4) * 4;
+                    float* stg = stages + slot * kTmaStageFloats;
+                    mbar_arrive_expect_tx(&full[slot], 4u * kTmaStageFloats);
+                    tma_load_3d(stg, &tmF, X0 + a.pp.ox, Y0 + a.pp.oy, i * NK + k, &full[slot]);
+                    tma_load_3d(stg + kTmaTH * kTmaTW, &tmB, X0 + a.pp.ox + base, Y0 + a.pp.oy - dy,
+                                ip * NK + k, &full[slot]);
+                    ++kk;
                 }
             }
+            if (!ok) s_abort = 1;
+            s_issued = kk;
+            s_uissued = nu;
         }
-        if (ok) {
-            float dsq = 0.f, nsq = 0.f;
-            bool bad = false;
+    } else {
+        const int tx = tid % 16, ty = tid / 16;
+        const size_t npx = (size_t)nx * ny;
+        const float k2 = a.k2;
+        float dsq = 0.f, nsq = 0.f;
+        bool bad = false, ok = true;
+        int kk = 0;
+        for (int t = t0, u = 0; t < t1 && ok; t += tstep, ++u) {
+            const int ub = u & 1;
+            const int tile = t / N, i = t % N;
+            const int x0 = (tile % tilesx) * kTmaTW + 4 * tx, y = (tile / tilesx) * kTmaTH + ty;
+            const bool rowin = x0 < nx && y < ny;
+            float af[4] = {0.f, 0.f, 0.f, 0.f}, zf[4] = {0.f, 0.f, 0.f, 0.f};
+            float ab[4] = {0.f, 0.f, 0.f, 0.f}, zb[4] = {0.f, 0.f, 0.f, 0.f};
+            float mfk[4], mbk[4];
+#pragma unroll
+            for (int p = 0; p < 4; ++p) {
+                const bool in = rowin && x0 + p < nx;
+                const size_t pix = (size_t)y * nx + x0 + p;
+                mfk[p] = in ? a.mins[i * npx + pix] * k2 : 0.f;
+                mbk[p] = in ? a.mins[(N + i) * npx + pix] * k2 : 0.f;
+            }
+            // window rows of this thread inside the neighbour tiles
+            const float* Un = utile + ub * 2 * kTmaUFloats + (ty + 7) * kTmaUW + 4 * tx + 8 - UOFF;
+            const float* Up = Un + kTmaUFloats;
+            if (!mbar_wait_bounded(&ufull[ub], (unsigned)((u >> 1) & 1))) {
+                s_abort = 1;
+                ok = false;
+                break;
+            }
+            for (int sy = 0; sy < W && ok; ++sy) {
+                const int dy = sy - RHO;
+                // window rows as float4 chunks, loaded when the sliding window
+                // first reaches them (forward slides right, backward left), so
+                // only two or three chunks of each are live at a time
+                const float4* rn = (const float4*)(Un + dy * kTmaUW);
+                const float4* rp = (const float4*)(Up - dy * kTmaUW);
+                float4 cn[NCH], cp[NCH];
+#pragma unroll
+                for (int sx = 0; sx < W; ++sx, ++kk) {
+                    const int dx = sx - RHO;
+                    const int slot = kk % kTmaStages;
+                    if (!mbar_wait_bounded(&full[slot], (unsigned)((kk / kTmaStages) & 1))) {
+                        s_abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    {
+                        const int flo = (UOFF + dx) >> 2, fhi = (UOFF + dx + 3) >> 2;
+                        const int blo = (UOFF - dx) >> 2, bhi = (UOFF - dx + 3) >> 2;
+                        const int pfhi = (UOFF + dx + 2) >> 2, pblo = (UOFF - dx + 1) >> 2;
+#pragma unroll
+                        for (int j = 0; j < NCH; ++j) {
+                            if ((sx == 0 && j >= flo && j <= fhi) || (sx > 0 && j == fhi && fhi != pfhi))
+                                cn[j] = rn[j];
+                            if ((sx == 0 && j >= blo && j <= bhi) || (sx > 0 && j == blo && blo != pblo))
+                                cp[j] = rp[j];
+                        }
+                    }
+                    const float* stg = stages + slot * kTmaStageFloats;
+                    const float4 f4 = *(const float4*)(stg + ty * kTmaTW + 4 * tx);
+                    const int off = -dx;
+                    const int base = off >= 0 ? (off / 4) * 4 : -(((-off) + 3) / 4) * 4;
+                    const int sh = off - base;
+                    const float* pb = stg + kTmaTH * kTmaTW + ty * kTmaBW + 4 * tx;
+                    const float4 b0 = *(const float4*)pb;
+                    const float4 b1 = *(const float4*)(pb + 4);
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&empty[slot]);   // this warp is done with the stage
+                    const float df[4] = {f4.x, f4.y, f4.z, f4.w};
+                    const float w8[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        const float ef = ex2_approx(fmaf(-df[p], k2, mfk[p]));
+                        const float eb = ex2_approx(fmaf(-w8[sh + p], k2, mbk[p]));
+                        af[p] = fmaf(ef, f4get(cn[(UOFF + p + dx) >> 2], (UOFF + p + dx) & 3), af[p]);
+                        ab[p] = fmaf(eb, f4get(cp[(UOFF + p - dx) >> 2], (UOFF + p - dx) & 3), ab[p]);
+                        zf[p] += ef;
+                        zb[p] += eb;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&uempty[ub]);   // this warp is done with the tile's windows
+            if (!ok) break;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const int x = x0 + p;
@@ -646,13 +765,13 @@ __global__ void __launch_bounds__(kTmaThreads) k_gj_tma(GjArgs a, const __grid_c
                     nsq = fmaf(fnew, fnew, nsq);
                 }
             }
-            if (bad) atomicOr(a.err, 8);
-            if (MODE == 1) {
-                const float d = warp_sum(dsq), n = warp_sum(nsq);
-                if (lane == 0) {
-                    wsum[0][warp] = (double)d;
-                    wsum[1][warp] = (double)n;
-                }
+        }
+        if (bad) atomicOr(a.err, 8);
+        if (MODE == 1) {
+            const float d = warp_sum(dsq), n = warp_sum(nsq);
+            if (lane == 0) {
+                wsum[0][warp] = (double)d;
+                wsum[1][warp] = (double)n;
             }
         }
     }
@@ -660,8 +779,11 @@ __global__ void __launch_bounds__(kTmaThreads) k_gj_tma(GjArgs a, const __grid_c
     if (s_abort) {
         if (tid == 0) {
             atomicOr(a.err, 16);
-            mbar_wait_bounded(ubar, 0u);
-            for (int kk = s_issued - kTmaStages; kk < s_issued; ++kk)   // drain copies in flight
+            // drain the block's copies in flight: the last use of each iterate
+            // buffer and the last kTmaStages stage loads
+            for (int u = max(0, s_uissued - 2); u < s_uissued; ++u)
+                mbar_wait_bounded(&ufull[u & 1], (unsigned)((u >> 1) & 1));
+            for (int kk = s_issued - kTmaStages; kk < s_issued; ++kk)
                 if (kk >= 0) mbar_wait_bounded(&full[kk % kTmaStages], (unsigned)((kk / kTmaStages) & 1));
         }
         __syncthreads();
@@ -679,11 +801,13 @@ __global__ void __launch_bounds__(kTmaThreads) k_gj_tma(GjArgs a, const __grid_c
 }
 
 static size_t tma_smem() {
-    return 128 + sizeof(float) * (kTmaStages * kTmaStageFloats + 2 * kTmaUFloats) + 16 * kTmaStages + 8;
+    return 128 + sizeof(float) * (kTmaStages * kTmaStageFloats + 4 * kTmaUFloats) +
+           8 * (2 * kTmaStages + 4);
 }
 
-// Opt the TMA sweeps into their dynamic shared memory (geometry creation).
-static cudaError_t prepare_gj_tma() {
+// Opt the TMA sweeps into their dynamic shared memory and count the CTAs the
+// device holds at once (geometry creation).
+static cudaError_t prepare_gj_tma(int* slots) {
     const int sm = (int)tma_smem();
     cudaError_t e = cudaSuccess;
 #define TNLM_PREP_GJ(W)                                                                     \
@@ -694,22 +818,41 @@ static cudaError_t prepare_gj_tma() {
     TNLM_PREP_GJ(3) TNLM_PREP_GJ(5) TNLM_PREP_GJ(7) TNLM_PREP_GJ(9) TNLM_PREP_GJ(11)
     TNLM_PREP_GJ(13) TNLM_PREP_GJ(15)
 #undef TNLM_PREP_GJ
-    return e;
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gj_tma<15, 1>, kTmaThreads,
+                                                           tma_smem())) != cudaSuccess)
+        return e;
+    *slots = (sms > 0 && per_sm > 0) ? sms * per_sm : 1;
+    return cudaSuccess;
+}
+
+// Tiles per CTA of the TMA sweep: one unless the autotuner measured more to
+// be faster on this device and shape.
+static int gj_tma_tpb(const tnlm_geometry* g) { return g->tune_gj_tpb > 0 ? g->tune_gj_tpb : 1; }
+static int gj_tma_blocks(const tnlm_geometry* g) {
+    const int tiles = ((g->nx + kTmaTW - 1) / kTmaTW) * ((g->ny + kTmaTH - 1) / kTmaTH) * g->N;
+    const int tpb = gj_tma_tpb(g);
+    return (tiles + tpb - 1) / tpb;
 }
 
 template <int MODE>
-static bool launch_gj_tma(const GjArgs& a, const Workspace& ws, int window, int nb, cudaStream_t st) {
+static bool launch_gj_tma(const tnlm_geometry* g, const GjArgs& a, const Workspace& ws, int window,
+                          cudaStream_t st) {
     const size_t sm = tma_smem();
     const CUtensorMap* U = a.uin == ws.U0 ? &ws.tmU0 : (a.uin == ws.U1 ? &ws.tmU1 : nullptr);
     if (!U) return false;
+    const int nb = gj_tma_blocks(g), tpb = gj_tma_tpb(g);
     switch (window) {
-        case 3: k_gj_tma<3, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
-        case 5: k_gj_tma<5, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
-        case 7: k_gj_tma<7, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
-        case 9: k_gj_tma<9, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
-        case 11: k_gj_tma<11, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
-        case 13: k_gj_tma<13, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
-        case 15: k_gj_tma<15, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U); return true;
+        case 3: k_gj_tma<3, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
+        case 5: k_gj_tma<5, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
+        case 7: k_gj_tma<7, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
+        case 9: k_gj_tma<9, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
+        case 11: k_gj_tma<11, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
+        case 13: k_gj_tma<13, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
+        case 15: k_gj_tma<15, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
         default: return false;
     }
 }
@@ -812,8 +955,9 @@ cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int win
                            (ws.pp.px % 4) == 0 && ws.pp.px >= tx64 + 2 * ws.pp.ox &&
                            ws.pp.py >= ty16 + 2 * ws.pp.oy;
     if (layout_ok && ws.tm_ok &&
-        (fout ? launch_gj_tma<1>(a, ws, window, nv, st) : launch_gj_tma<0>(a, ws, window, nv, st))) {
-        if (fout && ns > nv) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nv, 0, 16 * (size_t)(ns - nv), st);
+        (fout ? launch_gj_tma<1>(g, a, ws, window, st) : launch_gj_tma<0>(g, a, ws, window, st))) {
+        const int nt = gj_tma_blocks(g), nmax = ns > nv ? ns : nv;
+        if (fout && nmax > nt) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nt, 0, 16 * (size_t)(nmax - nt), st);
         return cudaGetLastError();
     }
     if (ws.pp.ox >= ((a.rho + 3) / 4) * 4 + 4 && ws.pp.oy >= a.rho && (ws.pp.px % 4) == 0 &&

@@ -10,10 +10,12 @@ surrounding lung (a small high-contrast structure on dark lung, as in the
 paper), ROI2 the spine disc against the surrounding soft tissue.  Both are
 eroded / kept away from edges by two pixels.
 
-    python -m paper_1009_1351_gb300.quality --case mid_a [--k 50]
+    python -m paper_1009_1351_gb300.quality --case mid_a [--k 50] [--sweep]
 
 reconstructs the slice by FBP and by the TNLM iteration on the GPU and
-prints the mean CNR of both ROIs and the mean SNR over the phases.
+prints the mean CNR of both ROIs and the mean SNR over the phases; --sweep
+adds the TNLM results over mu_hat in {0.25, 0.5, 1, 2} and h scaled by
+{0.5, 1, 2}.
 """
 from __future__ import annotations
 
@@ -91,6 +93,27 @@ def evaluate(c: synth.Case, f: np.ndarray, truth: np.ndarray) -> Dict[str, float
     return {k: float(np.mean(v)) for k, v in res.items()}
 
 
+MU_SWEEP = (0.25, 0.5, 1.0, 2.0)
+H_SCALE_SWEEP = (0.5, 1.0, 2.0)
+
+
+def sweep(c: synth.Case, d, geo, y, w, f0, k_outer: int):
+    """TNLM image quality over the grid mu_hat x h-scale (each from the FBP start)."""
+    import torch
+    import paper_1009_1351_gb300 as tn
+
+    rows = []
+    for mu in MU_SWEEP:
+        for hs in H_SCALE_SWEEP:
+            p = synth.Params(**{**c.params.__dict__, "k_outer": k_outer, "mu_hat": mu,
+                                "h": c.params.h * hs})
+            f = f0.clone()
+            tn.tnlm_reconstruct(geo, p, y, w, f)
+            torch.cuda.synchronize()
+            rows.append({"mu_hat": mu, "h": p.h, **evaluate(c, f.double().cpu().numpy(), d["truth"])})
+    return rows
+
+
 def main() -> None:
     import torch
     import paper_1009_1351_gb300 as tn
@@ -98,6 +121,7 @@ def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="mid_a")
     ap.add_argument("--k", type=int, default=None)
+    ap.add_argument("--sweep", action="store_true", help="also run the mu_hat x h grid")
     args = ap.parse_args()
     c = synth.case(args.case)
     d = synth.make_inputs(c)
@@ -109,6 +133,7 @@ def main() -> None:
     tn.tnlm_fbp(geo, y, f)
     torch.cuda.synchronize()
     fbp = f.double().cpu().numpy()
+    f_init = f.clone()
     tn.tnlm_reconstruct(geo, p, y, w, f)
     torch.cuda.synchronize()
     tnlm = f.double().cpu().numpy()
@@ -131,6 +156,8 @@ def main() -> None:
            "fbp_per_phase": evaluate(c, fbp_phase, d["truth"]),
            "fbp_all_views_init": evaluate(c, fbp, d["truth"]),
            "tnlm": evaluate(c, tnlm, d["truth"])}
+    if args.sweep:
+        out["sweep"] = sweep(c, d, geo, y, w, f_init, p.k_outer)
     print(json.dumps(out))
 
 

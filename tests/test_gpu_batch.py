@@ -1,0 +1,140 @@
+"""Batched reconstruction and the launch autotuner (GPU, through the C ABI).
+
+A batch must give every slice bitwise the result of its own
+tnlm_reconstruct call.  The autotuner's sweep tiling leaves results bitwise
+unchanged; its choice of backprojection view groups reorders FP32 sums, so
+results after it agree with the default to rounding (rel. L2 <= 1e-6).  One
+slice of the batch is also checked against the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+from paper_1009_1351_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REC_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def tn():
+    import paper_1009_1351_gb300 as tn
+    from paper_1009_1351_gb300 import build
+    build.build()
+    tn.load_library()
+    assert torch.cuda.is_available()
+    return tn
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def small_slices():
+    """Uneven slices: sizes, view counts, windows and iteration counts differ."""
+    out = []
+    specs = [(64, 48, 40, 96, 3, 5, 3), (48, 48, 24, 80, 3, 7, 4), (70, 52, 30, 110, 5, 5, 2),
+             (32, 40, 16, 64, 1, 3, 3)]
+    for k, (nx, ny, V, B, d, W, K) in enumerate(specs):
+        g = synth.Geometry(nx=nx, ny=ny, pixel_mm=64.0 / max(nx, ny), n_phases=4 + k % 2, n_views=V,
+                           n_bins=B, bin_mm=1.2, sid_mm=500.0, sdd_mm=800.0)
+        c = synth.Case(f"s{k}", g, synth.Params(patch=d, window=W, k_outer=K, m2=3, h=0.002 * d),
+                       1e4 * (k + 1), 1100 + k, k % 2 == 1)
+        out.append(c)
+    return out
+
+
+def inputs(c):
+    d = synth.make_inputs(c)
+    f0 = np.full((c.geom.n_phases, c.geom.ny, c.geom.nx), 0.01)
+    return d, f0
+
+
+def test_batch_matches_single_calls_bitwise(tn):
+    cases = small_slices()
+    geoms, ys, ws, fs, ref = [], [], [], [], []
+    for c in cases:
+        d, f0 = inputs(c)
+        g = tn.tnlm_create_geometry(c.geom)
+        f = dev(f0)
+        rep = tn.tnlm_reconstruct(g, c.params, dev(d["y"]), dev(d["w"]), f)
+        ref.append((f.clone(), rep))
+        geoms.append(tn.tnlm_create_geometry(c.geom))
+        ys.append(dev(d["y"]))
+        ws.append(dev(d["w"]))
+        fs.append(dev(f0))
+    reps = tn.tnlm_reconstruct_batch(geoms, [c.params for c in cases], ys, ws, fs, autotune=False)
+    torch.cuda.synchronize()
+    for c, f, (fr, rr), r in zip(cases, fs, ref, reps):
+        assert torch.equal(f, fr), c.name
+        assert r["iterations"] == c.params.k_outer
+        assert r["rel_change_hist"] == rr["rel_change_hist"]
+        assert r["residual_hist"] == rr["residual_hist"]
+    # a second call replays the cached graph and continues from the results
+    fs2 = [f.clone() for f in fs]
+    tn.tnlm_reconstruct_batch(geoms, [c.params for c in cases], ys, ws, fs2, autotune=False)
+    for c, g, y, w, f, f2 in zip(cases, geoms, ys, ws, fs, fs2):
+        f1 = f.clone()
+        tn.tnlm_reconstruct(g, c.params, y, w, f1)
+        assert torch.equal(f1, f2), c.name
+
+
+def test_batch_slice_matches_oracle(tn, oracle_mod):
+    c = small_slices()[1]
+    d, f0 = inputs(c)
+    others = small_slices()[2:]
+    geoms = [tn.tnlm_create_geometry(c.geom)] + [tn.tnlm_create_geometry(o.geom) for o in others]
+    ins = [(d, f0)] + [inputs(o) for o in others]
+    fs = [dev(x[1]) for x in ins]
+    tn.tnlm_reconstruct_batch(geoms, [c.params] + [o.params for o in others],
+                              [dev(x[0]["y"]) for x in ins], [dev(x[0]["w"]) for x in ins], fs)
+    torch.cuda.synchronize()
+    fo, _, _ = oracle_mod.reconstruct(oracle_mod.Geom(c.geom), d["y"], d["w"], f0, c.params)
+    got = fs[0].double().cpu().numpy()
+    err = np.linalg.norm(got - fo) / np.linalg.norm(fo)
+    assert err <= REC_TOL, err
+
+
+def test_autotune_choices_leave_results_unchanged(tn):
+    c = synth.case("tiny")
+    d = synth.make_inputs(c)
+    p = synth.Params(**{**c.params.__dict__, "k_outer": 3})
+    y, w = dev(d["y"]), dev(d["w"])
+    f0 = dev(np.full((c.geom.n_phases, c.geom.ny, c.geom.nx), 0.01))
+    g = tn.tnlm_create_geometry(c.geom)
+    f_default = f0.clone()
+    tn.tnlm_reconstruct(g, p, y, w, f_default)
+    keep = f0.clone()
+    choice = tn.tnlm_autotune(g, p, y, w, f0)
+    assert torch.equal(f0, keep)                       # the start image is untouched
+    assert 1 <= choice["bp_groups"] <= 4 and 1 <= choice["gj_tiles"] <= 3
+    f_tuned = f0.clone()
+    tn.tnlm_reconstruct(g, p, y, w, f_tuned)
+    a, b = f_tuned.double(), f_default.double()
+    assert float((a - b).norm() / b.norm()) <= 1e-6
+    f_again = f0.clone()
+    tn.tnlm_reconstruct(g, p, y, w, f_again)
+    assert torch.equal(f_again, f_tuned)               # deterministic under the choice
+    # a second handle of the same shape takes the cached choice
+    g2 = tn.tnlm_create_geometry(c.geom)
+    assert tn.tnlm_autotune(g2, p, y, w, f0) == choice
+
+
+def test_batch_rejects_tolerance_and_repeated_handles(tn):
+    import types
+    c = small_slices()[0]
+    d, f0 = inputs(c)
+    g = tn.tnlm_create_geometry(c.geom)
+    g2 = tn.tnlm_create_geometry(c.geom)
+    y, w, f = dev(d["y"]), dev(d["w"]), dev(f0)
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_reconstruct_batch([g, g], [c.params, c.params], [y, y], [w, w], [f, f.clone()])
+    assert e.value.status == tn.TNLM_ERR_INVALID_ARG
+    assert "repeats" in str(e.value)
+    p_tol = types.SimpleNamespace(**c.params.__dict__, tol=1e-3, tol_check_every=1)
+    with pytest.raises(tn.TnlmError) as e:
+        tn.tnlm_reconstruct_batch([g, g2], [c.params, p_tol], [y, y], [w, w], [f, f.clone()])
+    assert e.value.status == tn.TNLM_ERR_INVALID_ARG
+    assert "tol" in str(e.value)
+    assert torch.equal(f, dev(f0))                     # nothing ran
