@@ -145,6 +145,32 @@ def roofline_units(case, cls: str):
     return None, None, None
 
 
+def measured_traffic(cls: str, case_names):
+    """Mean DRAM bytes per launch of a kernel class over the given cases, from
+    the ncu captures listed in profiles/traffic.txt, or None when a case is
+    missing or the kernel's source file has changed since the capture."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    rows = {}
+    for line in open(path):
+        f = line.split()
+        if len(f) != 6 or line.startswith("#"):
+            continue
+        rows[(f[0], f[1])] = (int(f[2]) + int(f[3]), f[4], f[5])
+    vals = []
+    for c in case_names:
+        r = rows.get((cls, c))
+        if r is None:
+            return None
+        src = os.path.join(ROOT, r[1])
+        if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] != r[2]:
+            return None
+        vals.append(r[0])
+    return float(np.mean(vals))
+
+
 def fp32_peak_tflops():
     """FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock."""
     mhz = _peaks().get("sm_max_mhz", 2070.0)
@@ -279,9 +305,12 @@ def run_gpu(args):
                 achieved = amt / (per_launch_ms / 1e3) / 1e12
                 peak = fp32_peak_tflops()
                 src = "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+            traffic = measured_traffic(dominant, SCENARIOS)
             roof = {"bound": bound, "kernel": dominant, "achieved": round(achieved, 3),
                     "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
-                    "traffic": None, "peak_source": src, "launch_ms": round(per_launch_ms, 4)}
+                    "traffic": None if traffic is None else int(traffic),
+                    "traffic_unit": "DRAM bytes per launch (ncu, profiles/traffic.txt)",
+                    "peak_source": src, "launch_ms": round(per_launch_ms, 4)}
         # every kernel class, from the warm-up pass in which all classes were timed
         by_kernel = {}
         for cls in ("project", "backproject", "weights", "gj"):
@@ -294,8 +323,10 @@ def run_gpu(args):
                 ach, pk = amt_c / (ms_c / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0)
             else:
                 ach, pk = amt_c / (ms_c / 1e3) / 1e12, fp32_peak_tflops()
+            tr = measured_traffic(cls, SCENARIOS)
             by_kernel[cls] = {"bound": bound_c, "achieved": round(ach, 3), "peak": round(pk, 1),
-                              "unit": unit_c, "frac": round(ach / pk, 4), "launch_ms": round(ms_c, 4)}
+                              "unit": unit_c, "frac": round(ach / pk, 4), "launch_ms": round(ms_c, 4),
+                              "traffic": None if tr is None else int(tr)}
         out = {
             "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),

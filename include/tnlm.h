@@ -87,7 +87,13 @@ typedef struct {
     double tol;      /* > 0: stop once ||f^k - f^(k-1)|| / ||f^k|| < tol (checked on
                         the host every 'tol_check_every' iterations); 0: run K */
     int tol_check_every; /* >= 1 when tol > 0 */
+    int precision;   /* TNLM_PREC_FP32: every step in FP32 (FP64 reductions);
+                        TNLM_PREC_MIXED: the patch-distance cross terms of Eq. 8 as
+                        split-FP16 tensor-core products with FP32 accumulation
+                        (patch <= 5, window <= 11), all else as FP32 */
 } tnlm_params;
+
+enum { TNLM_PREC_FP32 = 0, TNLM_PREC_MIXED = 1 };
 
 /* Host-side report of tnlm_reconstruct (all FP64 values come from FP64
  * device reductions). */

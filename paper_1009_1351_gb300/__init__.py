@@ -32,6 +32,7 @@ EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tn
             "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp", "tnlm_autotune",
             "tnlm_reconstruct_batch")
 KCLASSES = ("prep", "project", "backproject", "cgls", "weights", "gj")
+PREC_FP32, PREC_MIXED = 0, 1
 
 
 class GeometryDesc(ctypes.Structure):
@@ -47,7 +48,7 @@ class ParamsC(ctypes.Structure):
                 ("patch", ctypes.c_int), ("window", ctypes.c_int), ("m1", ctypes.c_int),
                 ("m2", ctypes.c_int), ("k_outer", ctypes.c_int), ("data_step", ctypes.c_int),
                 ("clamp", ctypes.c_int), ("tol", ctypes.c_double),
-                ("tol_check_every", ctypes.c_int)]
+                ("tol_check_every", ctypes.c_int), ("precision", ctypes.c_int)]
 
 
 class ReportC(ctypes.Structure):
@@ -145,7 +146,8 @@ def params_c(p: Any) -> ParamsC:
     return ParamsC(float(p.mu_hat), float(p.h), float(getattr(p, "beta", 0.0)), int(p.patch),
                    int(p.window), int(p.m1), int(p.m2), int(p.k_outer),
                    int(getattr(p, "data_step", 0)), int(getattr(p, "clamp", 1)),
-                   float(getattr(p, "tol", 0.0)), int(getattr(p, "tol_check_every", 1)))
+                   float(getattr(p, "tol", 0.0)), int(getattr(p, "tol_check_every", 1)),
+                   int(getattr(p, "precision", PREC_FP32)))
 
 
 class Geometry:

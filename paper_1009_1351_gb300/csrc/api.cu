@@ -135,6 +135,10 @@ tnlm_status check_params(const tnlm_params* p) {
     if (!(p->tol >= 0.0) || !isfinite(p->tol)) return fail(TNLM_ERR_INVALID_ARG, "tol must be >= 0");
     if (p->tol > 0.0 && p->tol_check_every < 1)
         return fail(TNLM_ERR_INVALID_ARG, "tol_check_every must be >= 1 when tol > 0");
+    if (p->precision != TNLM_PREC_FP32 && p->precision != TNLM_PREC_MIXED)
+        return fail(TNLM_ERR_INVALID_ARG, "precision must be TNLM_PREC_FP32 or TNLM_PREC_MIXED");
+    if (p->precision == TNLM_PREC_MIXED && !weights_tc_supported(p->patch, p->window))
+        return fail(TNLM_ERR_INVALID_ARG, "mixed precision supports patch <= 5 and window in [3, 11]");
     return TNLM_OK;
 }
 
@@ -289,7 +293,10 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     }
     // ---- TNLM step: weights from g = ws.u, Gauss-Jacobi, positivity
     if (p->m2 > 0) {
-        LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, ws, p->patch, p->window, ws.u, st), "weights");
+        if (p->precision == TNLM_PREC_MIXED)
+            LK(TNLM_KCLASS_WEIGHTS, launch_weights_tc(g, ws, p->patch, p->window, ws.u, st), "weights (tensor cores)");
+        else
+            LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, ws, p->patch, p->window, ws.u, st), "weights");
         float* bufs[2] = {ws.U0, ws.U1};
         for (int m = 0; m < p->m2; ++m) {
             const bool last = m == p->m2 - 1;
@@ -323,7 +330,7 @@ struct GraphState {
 bool same_shape(const tnlm_params& a, const tnlm_params& b) {
     return a.mu_hat == b.mu_hat && a.h == b.h && a.beta == b.beta && a.patch == b.patch &&
            a.window == b.window && a.m1 == b.m1 && a.m2 == b.m2 && a.data_step == b.data_step &&
-           a.clamp == b.clamp;
+           a.clamp == b.clamp && a.precision == b.precision;
 }
 
 tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f) {
@@ -738,6 +745,8 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
     }
     e = prepare_backproject(&g->cta_slots_bp);
     if (e == cudaSuccess) e = prepare_weights(&g->cta_slots_gj);
+    if (e == cudaSuccess) e = prepare_weights_tc();
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) {
         tnlm_destroy_geometry(g);
         return cuda_fail(e, "kernel attributes");
@@ -916,7 +925,10 @@ tnlm_status tnlm_weights(const tnlm_geometry* gc, const tnlm_params* p, const fl
     cudaStream_t st = (cudaStream_t)stream;
     s = ensure_ws(g, (p->window - 1) / 2, g->ws.base ? g->ws.kcap : 1, st);
     if (s != TNLM_OK) return s;
-    LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, g->ws, p->patch, p->window, d_g, st), "weights");
+    if (p->precision == TNLM_PREC_MIXED)
+        LK(TNLM_KCLASS_WEIGHTS, launch_weights_tc(g, g->ws, p->patch, p->window, d_g, st), "weights (tensor cores)");
+    else
+        LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, g->ws, p->patch, p->window, d_g, st), "weights");
     LK(TNLM_KCLASS_WEIGHTS, launch_weights_norm(g, g->ws, p->window, p->h, st), "weights normalisers");
     LK(TNLM_KCLASS_WEIGHTS, launch_weights_export(g, g->ws, p->window, d_dist, d_norm, st), "weights export");
     return TNLM_OK;

@@ -95,6 +95,7 @@ struct tnlm_geometry {
     tnlm::Workspace ws;
     int cta_slots_bp = 0;       // resident backprojector CTAs on the device
     int cta_slots_gj = 0;       // resident TMA-sweep CTAs on the device
+    int num_sms = 0;            // streaming multiprocessors of the device
     // launch choices set by tnlm_autotune (0 = built-in heuristic); tune_gen
     // changes whenever they do, so captured graphs are re-captured
     int tune_bp_groups = 0;     // view groups (CTAs) per backprojection tile
@@ -127,7 +128,11 @@ cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R,
 cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
                            const ProjOut& o, cudaStream_t st);
 cudaError_t prepare_backproject(int* slots);
-cudaError_t prepare_weights(int* gj_slots);   // also counts resident TMA-sweep CTAs
+cudaError_t prepare_weights(int* gj_slots);
+cudaError_t prepare_weights_tc();                 // tensor-core variant (mixed precision)
+bool weights_tc_supported(int patch, int window);
+cudaError_t launch_weights_tc(const tnlm_geometry* g, const Workspace& ws, int patch, int window,
+                              const float* gimg, cudaStream_t st);   // also counts resident TMA-sweep CTAs
 int bp_blocks_per_phase(const tnlm_geometry* g);
 int bp_max_groups(const tnlm_geometry* g);      // largest useful view-group count
 size_t static_scratch_floats();
@@ -203,4 +208,39 @@ __device__ __forceinline__ float ex2_approx(float x) {
     return y;
 }
 
+// ---------------------------------------------------------------------------
+// mbarrier helpers (shared by the TMA sweep and the tensor-core weights).
+// Every wait is bounded: after kSpinLimit polls it gives up and returns false.
+// ---------------------------------------------------------------------------
+constexpr long kSpinLimit = 1L << 24;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    for (long it = 0; it < kSpinLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
 }  // namespace tnlm

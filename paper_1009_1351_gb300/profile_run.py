@@ -1,6 +1,6 @@
 """Run one named workload through the library, for profilers (ncu) and timing.
 
-    python -m paper_1009_1351_gb300.profile_run --case mid_a --k 1 [--m1 3 --m2 5] [--ops 10]
+    python -m paper_1009_1351_gb300.profile_run --case mid_a --k 1 [--m1 3 --m2 5] [--ops 10] [--mixed]
 
 Builds the seeded inputs of the workload, runs tnlm_reconstruct with K outer
 iterations from the constant start image, then --ops projections and --ops
@@ -25,6 +25,7 @@ def main() -> None:
     ap.add_argument("--m2", type=int, default=None)
     ap.add_argument("--ops", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--mixed", action="store_true", help="tensor-core patch distances")
     args = ap.parse_args()
     c = synth.case(args.case)
     d = synth.make_inputs(c)
@@ -33,6 +34,8 @@ def main() -> None:
         over["m1"] = args.m1
     if args.m2 is not None:
         over["m2"] = args.m2
+    if args.mixed:
+        over["precision"] = tn.PREC_MIXED
     p = synth.Params(**{**c.params.__dict__, **over})
     geo = tn.tnlm_create_geometry(c.geom)
     dv = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")

@@ -74,6 +74,7 @@ class Params:
     k_outer: int = 20         # outer iterations
     data_step: int = 0        # 0 = CGLS, 1 = gradient step (Eq. 4)
     clamp: int = 1            # positivity truncation after each outer iteration
+    precision: int = 0        # 0: FP32; 1: split-FP16 tensor-core patch cross terms
 
 
 @dataclasses.dataclass(frozen=True)
