@@ -161,6 +161,12 @@ tnlm_status tnlm_backproject(const tnlm_geometry* geom, const float* d_sino, flo
  * same image.  Uses the handle's workspace (allocated on first use). */
 tnlm_status tnlm_fbp(const tnlm_geometry* geom, const float* d_y, float* d_img, void* stream);
 
+/* FBP of each phase from its own V views only (the same filter, dbeta =
+ * 2 pi / V): d_img[i] reconstructs phase i.  This is the per-phase FBP the
+ * paper compares against (Sec. 3) and the input of the learned warm start.
+ * Layout, ownership and errors as tnlm_fbp. */
+tnlm_status tnlm_fbp_phases(const tnlm_geometry* geom, const float* d_y, float* d_img, void* stream);
+
 /* Byte sizes of the two output buffers of tnlm_weights. */
 tnlm_status tnlm_weights_size(const tnlm_geometry* geom, const tnlm_params* params,
                               size_t* dist_bytes, size_t* norm_bytes);

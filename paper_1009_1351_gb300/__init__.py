@@ -30,7 +30,9 @@ EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tn
             "tnlm_weights_size", "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct",
             "tnlm_last_error", "tnlm_debug_fail_alloc_after", "tnlm_profile_enable",
             "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp", "tnlm_autotune",
-            "tnlm_reconstruct_batch")
+            "tnlm_reconstruct_batch", "tnlm_fbp_phases", "tnlm_unet_create", "tnlm_unet_destroy", "tnlm_unet_param_count",
+            "tnlm_unet_set_params", "tnlm_unet_get_params", "tnlm_unet_forward", "tnlm_unet_grads",
+            "tnlm_unet_adam_step", "tnlm_unet_last_error")
 KCLASSES = ("prep", "project", "backproject", "cgls", "weights", "gj")
 PREC_FP32, PREC_MIXED = 0, 1
 
@@ -83,6 +85,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_backproject.argtypes = [vp, vp, vp, vp]
     lib.tnlm_project_static.argtypes = [vp, vp, vp, vp]
     lib.tnlm_fbp.argtypes = [vp, vp, vp, vp]
+    lib.tnlm_fbp_phases.argtypes = [vp, vp, vp, vp]
     lib.tnlm_weights_size.argtypes = [vp, ctypes.POINTER(ParamsC), ctypes.POINTER(ctypes.c_size_t),
                                       ctypes.POINTER(ctypes.c_size_t)]
     lib.tnlm_weights.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp, vp]
@@ -94,6 +97,19 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_reconstruct_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ParamsC), ctypes.c_int,
                                            ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                            ctypes.POINTER(ReportC), ctypes.c_int, vp]
+    lib.tnlm_unet_create.argtypes = [ctypes.c_int] * 5 + [ctypes.POINTER(vp)]
+    lib.tnlm_unet_destroy.argtypes = [vp]
+    lib.tnlm_unet_destroy.restype = None
+    lib.tnlm_unet_param_count.argtypes = [vp]
+    lib.tnlm_unet_param_count.restype = ctypes.c_longlong
+    lib.tnlm_unet_set_params.argtypes = [vp, vp]
+    lib.tnlm_unet_get_params.argtypes = [vp, vp, vp]
+    lib.tnlm_unet_forward.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp]
+    lib.tnlm_unet_grads.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), vp]
+    lib.tnlm_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                        ctypes.c_float, vp]
+    lib.tnlm_unet_last_error.restype = ctypes.c_char_p
     lib.tnlm_last_error.restype = ctypes.c_char_p
     lib.tnlm_debug_fail_alloc_after.argtypes = [ctypes.c_int]
     lib.tnlm_debug_fail_alloc_after.restype = None
@@ -204,6 +220,11 @@ def tnlm_project_static(geom: Geometry, img, sino, stream=None) -> None:
 def tnlm_fbp(geom: Geometry, y, img, stream=None) -> None:
     """Initial image: fan-beam FBP of all phases' projections (every phase the same)."""
     _check(load_library().tnlm_fbp(geom.handle, _ptr(y), _ptr(img), _stream(stream)))
+
+
+def tnlm_fbp_phases(geom: Geometry, y, img, stream=None) -> None:
+    """Per-phase fan-beam FBP: phase i from its own views only."""
+    _check(load_library().tnlm_fbp_phases(geom.handle, _ptr(y), _ptr(img), _stream(stream)))
 
 
 def tnlm_backproject(geom: Geometry, sino, img, stream=None) -> None:
@@ -317,3 +338,64 @@ def tnlm_profile_read(geom: Geometry, reset: bool = True) -> Dict[str, Dict[str,
     n = (ctypes.c_longlong * len(KCLASSES))()
     _check(load_library().tnlm_profile_read(geom.handle, ms, n, 1 if reset else 0))
     return {c: {"ms": ms[k], "launches": int(n[k])} for k, c in enumerate(KCLASSES)}
+
+
+# ---------------------------------------------------------------------------
+# learned warm start (include/tnlm_unet.h)
+# ---------------------------------------------------------------------------
+def _ucheck(status: int) -> None:
+    if status != TNLM_OK:
+        msg = load_library().tnlm_unet_last_error().decode(errors="replace")
+        raise TnlmError(status, msg)
+
+
+class UNet:
+    """Owns a tnlm_unet (2D U-Net over phases as channels, BF16 storage)."""
+
+    def __init__(self, in_ch: int = 10, out_ch: int = 10, base: int = 32, levels: int = 4,
+                 device: int = 0):
+        self.in_ch, self.out_ch, self.base, self.levels = in_ch, out_ch, base, levels
+        h = ctypes.c_void_p()
+        _ucheck(load_library().tnlm_unet_create(in_ch, out_ch, base, levels, device, ctypes.byref(h)))
+        self.handle = h.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.tnlm_unet_destroy(self.handle)
+            self.handle = None
+
+    @property
+    def param_count(self) -> int:
+        return int(load_library().tnlm_unet_param_count(self.handle))
+
+    def set_params(self, flat) -> None:
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        if a.size != self.param_count:
+            raise ValueError(f"expected {self.param_count} parameters, got {a.size}")
+        _ucheck(load_library().tnlm_unet_set_params(self.handle, a.ctypes.data))
+
+    def get_params(self, grads: bool = False):
+        import numpy as np
+        n = self.param_count
+        p = np.zeros(n, dtype=np.float32)
+        g = np.zeros(n, dtype=np.float32) if grads else None
+        _ucheck(load_library().tnlm_unet_get_params(self.handle, p.ctypes.data,
+                                                    g.ctypes.data if grads else None))
+        return (p, g) if grads else p
+
+    def forward(self, x, out, stream=None) -> None:
+        b, c, h, w = x.shape
+        _ucheck(load_library().tnlm_unet_forward(self.handle, _ptr(x), _ptr(out), b, h, w,
+                                                 _stream(stream)))
+
+    def grads(self, x, target, stream=None) -> float:
+        b, c, h, w = x.shape
+        loss = ctypes.c_double(0.0)
+        _ucheck(load_library().tnlm_unet_grads(self.handle, _ptr(x), _ptr(target), b, h, w,
+                                               ctypes.byref(loss), _stream(stream)))
+        return loss.value
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+                  stream=None) -> None:
+        _ucheck(load_library().tnlm_unet_adam_step(self.handle, lr, beta1, beta2, eps, _stream(stream)))

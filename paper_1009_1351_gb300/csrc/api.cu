@@ -888,6 +888,21 @@ tnlm_status tnlm_fbp(const tnlm_geometry* gc, const float* d_y, float* d_img, vo
     return TNLM_OK;
 }
 
+tnlm_status tnlm_fbp_phases(const tnlm_geometry* gc, const float* d_y, float* d_img, void* stream) {
+    g_err[0] = 0;
+    if (check_geom_handle(gc) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
+    if (!d_y || !d_img) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
+    if (!aligned16(d_y) || !aligned16(d_img)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
+    tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
+    DeviceGuard dg(g->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t st = (cudaStream_t)stream;
+    tnlm_status s = ensure_ws(g, g->ws.base ? g->ws.rho : 0, g->ws.base ? g->ws.kcap : 1, st);
+    if (s != TNLM_OK) return s;
+    LK(TNLM_KCLASS_PREP, launch_fbp_phases(g, d_y, g->ws.t, d_img, st), "fbp per phase");
+    return TNLM_OK;
+}
+
 tnlm_status tnlm_weights_size(const tnlm_geometry* g, const tnlm_params* p, size_t* dist_bytes,
                               size_t* norm_bytes) {
     g_err[0] = 0;

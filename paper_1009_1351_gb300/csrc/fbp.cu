@@ -69,6 +69,53 @@ __global__ void __launch_bounds__(256) k_fbp_backproject(const float* __restrict
     for (int i = 0; i < N; ++i) img[i * npx + (size_t)iy * nx + ix] = acc;
 }
 
+// Per-phase variant: phase i is reconstructed from its own V views only
+// (dbeta = 2 pi / V), one grid layer per phase.
+__global__ void __launch_bounds__(256) k_fbp_backproject_phase(const float* __restrict__ Q,
+                                                               const float2* __restrict__ view,
+                                                               float* __restrict__ img, int nx, int ny,
+                                                               int V, int B, float sidp, float inv_dg,
+                                                               float half_b, float scale) {
+    const int ix = blockIdx.x * 16 + (threadIdx.x & 15);
+    const int iy = blockIdx.y * 16 + (threadIdx.x >> 4);
+    const int i = blockIdx.z;
+    if (ix >= nx || iy >= ny) return;
+    const float cx = (float)ix - 0.5f * (nx - 1);
+    const float cy = (float)iy - 0.5f * (ny - 1);
+    float acc = 0.f;
+    for (int v = i * V; v < (i + 1) * V; ++v) {
+        const float2 vt = view[v];
+        const float X = vt.y * cx - vt.x * cy;
+        const float Y = sidp - (vt.x * cx + vt.y * cy);
+        const float u = fmaf(atanf(X / Y), inv_dg, half_b);
+        const float fl = floorf(u);
+        const int k0 = (int)fl;
+        const float t = u - fl;
+        const float* q = Q + (size_t)v * B;
+        float val = 0.f;
+        if (k0 >= 0 && k0 < B) val = (1.f - t) * __ldg(q + k0);
+        if (k0 + 1 >= 0 && k0 + 1 < B) val = fmaf(t, __ldg(q + k0 + 1), val);
+        acc += val / fmaf(X, X, Y * Y);
+    }
+    img[((size_t)i * ny + iy) * nx + ix] = acc * scale;
+}
+
+cudaError_t launch_fbp_phases(const tnlm_geometry* g, const float* y, float* Q, float* img,
+                              cudaStream_t st) {
+    const int M = g->N * g->V;
+    const float dg = (float)(g->bin_mm / g->sdd);
+    const size_t smem = sizeof(float) * (3 * (size_t)g->B - 1);
+    k_fbp_filter<<<M, 256, smem, st>>>(y, g->d_fbp_taps, g->d_bin, Q, g->B, (float)g->sid, dg);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const double scale = 2.0 * 3.14159265358979323846 / (double)g->V / (g->pixel * g->pixel);
+    dim3 grid((g->nx + 15) / 16, (g->ny + 15) / 16, g->N);
+    k_fbp_backproject_phase<<<grid, 256, 0, st>>>(Q, g->d_view, img, g->nx, g->ny, g->V, g->B,
+                                                  (float)(g->sid / g->pixel), (float)(g->sdd / g->bin_mm),
+                                                  0.5f * (float)(g->B - 1), (float)scale);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fbp(const tnlm_geometry* g, const float* y, float* Q, float* img,
                        cudaStream_t st) {
     const int M = g->N * g->V;

@@ -145,6 +145,8 @@ cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float*
 // initial image (filtered backprojection of all views); Q: [N*V*B] scratch
 cudaError_t launch_fbp(const tnlm_geometry* g, const float* y, float* Q, float* img,
                        cudaStream_t st);
+cudaError_t launch_fbp_phases(const tnlm_geometry* g, const float* y, float* Q, float* img,
+                              cudaStream_t st);
 
 // CGLS vector / scalar kernels
 cudaError_t launch_cgls_init_scalars(const tnlm_geometry* g, const Workspace& ws,

@@ -22,7 +22,8 @@ def lib():
 
 
 def header_functions():
-    src = open(os.path.join(ROOT, "include", "tnlm.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(tnlm_[a-z_0-9]+)\s*\(", src)))
 
