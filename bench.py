@@ -178,6 +178,24 @@ def fp32_peak_tflops():
 
 
 # ---------------------------------------------------------------------------
+# multi-rank aggregation (replicas: every rank reconstructs its own slices)
+# ---------------------------------------------------------------------------
+def max_over_ranks(vals, dev, world: int):
+    """Element-wise maximum over all ranks (the slowest rank sets the time)."""
+    import torch
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t]
+
+
+def job_throughput(slices_per_rank: int, steps: int, world: int, max_ms: float) -> float:
+    """Whole-job slices per second: all ranks' slices over the slowest rank's time."""
+    return slices_per_rank * steps * world / (max_ms / 1e3)
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 def run_gpu(args):
@@ -279,13 +297,10 @@ def run_gpu(args):
         h2d += (s["hy"].numel() + s["hw"].numel()) * 4
         d2h += s["hout"].numel() * 4
 
-    t = torch.tensor([total_ms, statistics.median(e2e_times)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, e2e_s = float(t[0]), float(t[1])
+    total_ms, e2e_s = max_over_ranks([total_ms, statistics.median(e2e_times)], dev, world)
     n_slices = len(slices)
-    value = n_slices * args.steps * world / (total_ms / 1e3)
-    e2e_value = n_slices * world / e2e_s
+    value = job_throughput(n_slices, args.steps, world, total_ms)
+    e2e_value = job_throughput(n_slices, 1, world, e2e_s * 1e3)
 
     if rank == 0:
         amount, unit, bound = roofline_units(cases[0], dominant)
@@ -416,8 +431,9 @@ def run_batch(args):
            "data": "synthetic (seeded ellipse phantom, analytic line integrals, Poisson noise)",
            "config": {"workload": (f"batch of {n} 10-phase slices per step, sides from 256/384/512 "
                                    "(384 mm field), 60/90/180/360 views, I0 log-uniform 5e3..1e6, "
-                                   "d/W 5/11 (7/15 at 512), K=50, FBP start; one graph per outer "
-                                   "iteration for all slices (tnlm_reconstruct_batch)"),
+                                   "d=5, W=11, K=50, FBP start, tensor-core (split-FP16) patch "
+                                   "distances; one graph per outer iteration for all slices "
+                                   "(tnlm_reconstruct_batch), launch shapes autotuned"),
                       "slices": sizes, "autotuned": {f"{k[0]}^2/{k[1]}v": v for k, v in tuned.items()},
                       "l2": "inputs far larger than L2", "parallelism": "batch x1"},
            "clocks": clk, "e2e": None, "cpu_baseline": None,

@@ -133,16 +133,17 @@ BATCH_VIEWS = (60, 90, 180, 360)
 BATCH_BINS = {256: 512, 384: 700, 512: 888}
 
 
-def batch_cases(n: int = 64, seed: int = 1040, k_outer: int = 50
+def batch_cases(n: int = 64, seed: int = 1040, k_outer: int = 50, precision: int = 1
                 ) -> List[Tuple[Case, Tuple[float, float]]]:
     """The batched workload: n independent 10-phase slices.
 
     Side L drawn uniformly from {256, 384, 512} (pixel 384 mm / L, so every
     slice covers the same 384 mm field), views per phase from {60, 90, 180,
     360}, I0 log-uniform in [5e3, 1e6], the anatomy shifted by up to 5 % of L
-    along each axis; 1 mm bins (512 / 700 / 888 of them); d = 5, W = 11 below
-    512 and d = 7, W = 15 at 512 (the patch / window pairs of the 256^2 and
-    512^2 workloads).  Returns (case, anatomy offset in pixels) per slice.
+    along each axis; 1 mm bins (512 / 700 / 888 of them); d = 5, W = 11 (the
+    256^2 workload's patch and window) and, by default, the mixed-precision
+    patch distances (precision = 1).  Returns (case, anatomy offset in
+    pixels) per slice.
     """
     rng = np.random.default_rng(seed)
     out = []
@@ -151,9 +152,10 @@ def batch_cases(n: int = 64, seed: int = 1040, k_outer: int = 50
         V = int(rng.choice(BATCH_VIEWS))
         i0 = float(math.exp(rng.uniform(math.log(5e3), math.log(1e6))))
         off = (float(rng.uniform(-0.05, 0.05) * L), float(rng.uniform(-0.05, 0.05) * L))
-        d, W = (7, 15) if L == 512 else (5, 11)
+        d, W = 5, 11
         c = Case(f"batch{i:02d}", _geom(L, 384.0 / L, V, BATCH_BINS[L], 1.0),
-                 Params(patch=d, window=W, k_outer=k_outer, m2=5, h=0.002 * d), i0, seed + 1 + i, True)
+                 Params(patch=d, window=W, k_outer=k_outer, m2=5, h=0.002 * d, precision=precision),
+                 i0, seed + 1 + i, True)
         out.append((c, off))
     return out
 

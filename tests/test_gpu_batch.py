@@ -138,3 +138,37 @@ def test_batch_rejects_tolerance_and_repeated_handles(tn):
     assert e.value.status == tn.TNLM_ERR_INVALID_ARG
     assert "tol" in str(e.value)
     assert torch.equal(f, dev(f0))                     # nothing ran
+
+
+def test_batch_workload_sampled_slices_match_oracle(tn, oracle_mod):
+    """Four slices sampled from the 64-slice batched workload (one per side
+    length and a 60-view one), mixed-precision patch distances, batched and
+    autotuned, after K = 2 outer iterations: relative L2 <= 1e-3 against the
+    FP64 oracle (the workload's accuracy bound)."""
+    items = synth.batch_cases(64)
+    pick, seen = [], set()
+    for i, (c, _) in enumerate(items):
+        if c.geom.nx not in seen:
+            seen.add(c.geom.nx)
+            pick.append(i)
+    pick.append(next(i for i, (c, _) in enumerate(items) if c.geom.n_views == 60 and i not in pick))
+    geoms, ps, ys, ws, fs, ins = [], [], [], [], [], []
+    for i in pick:
+        c, off = items[i]
+        d = synth.make_inputs(c, off)
+        p = synth.Params(**{**c.params.__dict__, "k_outer": 2})
+        f0 = np.full((c.geom.n_phases, c.geom.ny, c.geom.nx), 0.01)
+        geoms.append(tn.tnlm_create_geometry(c.geom))
+        ps.append(p)
+        ys.append(dev(d["y"]))
+        ws.append(dev(d["w"]))
+        fs.append(dev(f0))
+        ins.append((c, d, f0, p))
+    tn.tnlm_reconstruct_batch(geoms, ps, ys, ws, fs, autotune=True)
+    torch.cuda.synchronize()
+    for (c, d, f0, p), f in zip(ins, fs):
+        ref, _, _ = oracle_mod.reconstruct(oracle_mod.Geom(c.geom), d["y"].astype(np.float32),
+                                           d["w"].astype(np.float32), f0.astype(np.float32), p)
+        got = f.double().cpu().numpy()
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err <= 1e-3, (c.name, err)
