@@ -33,7 +33,8 @@ constexpr int kTcTW = 16, kTcTH = 8;      // pixel tile (M = 128)
 constexpr int kTcNHalf = 240;              // N of one MMA; two of them
 constexpr int kTcN = 2 * kTcNHalf;
 constexpr int kTcKB = 32;                  // K of one hi or lo operand block (d*d <= 25, zero padded)
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
+constexpr int kTcWG = kTcThreads / 128;      // warpgroups; each reads all 128 accumulator lanes
 constexpr int kTcRowBytes = kTcKB * 2;     // one operand row of a block: 64 bytes
 constexpr int kTcSBO = (kTcKB / 8) * 128;  // byte step between 8-row groups (4 core matrices of 128 B)
 constexpr float kTcScale = 1024.f;
@@ -43,15 +44,15 @@ constexpr int kTcAhi = 0;
 constexpr int kTcAlo = kTcAhi + 128 * kTcRowBytes;           // 8 KB each
 constexpr int kTcBhi = kTcAlo + 128 * kTcRowBytes;
 constexpr int kTcBlo = kTcBhi + kTcN * kTcRowBytes;           // 30 KB each
-constexpr int kTcStage = kTcBlo + kTcN * kTcRowBytes;         // 8 warps x 32 x 32 floats
-constexpr int kTcGi = kTcStage + 8 * 32 * 32 * 4;             // FP32 tile of g_i (<= 20 x 12)
+constexpr int kTcStage = kTcBlo + kTcN * kTcRowBytes;         // per warp 32 x 32 floats
+constexpr int kTcGi = kTcStage + (kTcThreads / 32) * 32 * 32 * 4;  // FP32 tile of g_i (<= 20 x 12)
 constexpr int kTcGj = kTcGi + 256 * 4;                        // FP32 region of g_j (<= 30 x 22)
 constexpr int kTcHiLo = kTcGj + 672 * 4;                      // FP16 hi / lo of both (2 x (256 + 672))
 constexpr int kTcNa = kTcHiLo + 2 * (256 + 672) * 2;
 constexpr int kTcNb = kTcNa + 128 * 4;
 constexpr int kTcBM = kTcNb + kTcN * 4;                       // backward minima (<= 26 x 18)
-constexpr int kTcMf = kTcBM + 480 * 4;                        // forward minima of the two warpgroups
-constexpr int kTcBar = kTcMf + 2 * 128 * 4;
+constexpr int kTcMf = kTcBM + 480 * 4;                        // forward minima of each warpgroup
+constexpr int kTcBar = kTcMf + kTcWG * 128 * 4;
 constexpr int kTcBytes = kTcBar + 16;
 static_assert(kTcBytes + 1024 > 116 * 1024, "one CTA per SM keeps all of tensor memory free");
 
@@ -177,7 +178,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_weights_tc(TcArgs a) {
     const int q = warp & 3, wg = warp >> 2;
     const int m = 32 * q + lane, px = m & 15, py = m >> 4;
     constexpr int NROW = 2 * RHO + 2;
-    const int cr0 = 2 * q + wg * ((NROW + 1) / 2), cr1 = 2 * q + (wg ? NROW : (NROW + 1) / 2);
+    constexpr int RPW = (NROW + kTcWG - 1) / kTcWG;    // candidate rows per warpgroup
+    const int cr0 = 2 * q + min(NROW, wg * RPW), cr1 = 2 * q + min(NROW, (wg + 1) * RPW);
     float* stg = stage + warp * 32 * 32;
     unsigned phase = 0;
 
@@ -323,7 +325,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_weights_tc(TcArgs a) {
         // forward minima of the tile's pixels, backward minima of its reach
         if (tid < 128) {
             const int xm = X0 + (tid & 15), ym = Y0 + (tid >> 4);
-            const float v = fminf(mfp[tid], mfp[128 + tid]);
+            float v = mfp[tid];
+#pragma unroll
+            for (int w2 = 1; w2 < kTcWG; ++w2) v = fminf(v, mfp[w2 * 128 + tid]);
             if (xm < nx && ym < ny) {
                 a.mins[p * npx + (size_t)ym * nx + xm] = v;
                 if (!(v < INFINITY)) atomicOr(a.err, 4);

@@ -13,9 +13,9 @@ FBP of all views, box step 1) and decides the result.
    anatomy shifted by up to 5 % of the side), its sinogram P f* (the
    library's projector) with Poisson noise in one of the three dose
    scenarios of the 256^2 workload, the per-phase FBP (input) and the TNLM
-   result after K = 50 outer iterations from the all-views FBP (target).
-   Slices of one scenario are reconstructed together with
-   tnlm_reconstruct_batch.
+   result from the all-views FBP (target): run to the stopping tolerance
+   (--target-tol) or for K = 50 outer iterations (slices of one scenario
+   then run together with tnlm_reconstruct_batch).
 2. Training: mean squared error, Adam, images scaled by 50 (unit order).
 3. Evaluation on held-out seeds: iterations to the stopping tolerance
    (relative change of f below tol), device time and the error of the final
@@ -78,8 +78,8 @@ def phantom_gpu(torch, c: synth.Case, offset, dev, ss: int = 4):
 class PairMaker:
     """Makes (per-phase FBP, all-views FBP, TNLM target, truth) on the GPU."""
 
-    def __init__(self, torch, tn, slots: int = 16, k_outer: int = 50):
-        self.torch, self.tn, self.k = torch, tn, k_outer
+    def __init__(self, torch, tn, slots: int = 16, k_outer: int = 50, tol: float = 0.0):
+        self.torch, self.tn, self.k, self.tol = torch, tn, k_outer, tol
         self.dev = torch.device("cuda")
         self.cases = {s: synth.case(s) for s in SCENARIOS}
         self.geos = {s: [tn.tnlm_create_geometry(self.cases[s].geom) for _ in range(slots)]
@@ -120,7 +120,15 @@ class PairMaker:
                     out["scenario"].append(sc)
                     out["seed"].append(sd)
                     ys.append(y); ws.append(lam); fs.append(f)
-                tn.tnlm_reconstruct_batch(self.geos[sc][:len(chunk)], p, ys, ws, fs)
+                if self.tol > 0.0:
+                    # targets converged to the stopping tolerance, one slice at a time
+                    import types
+                    pt = types.SimpleNamespace(**p.__dict__, tol=self.tol, tol_check_every=1)
+                    for j in range(len(chunk)):
+                        rep = tn.tnlm_reconstruct(self.geos[sc][j], pt, ys[j], ws[j], fs[j])
+                        out.setdefault("target_iters", []).append(rep["iterations"])
+                else:
+                    tn.tnlm_reconstruct_batch(self.geos[sc][:len(chunk)], p, ys, ws, fs)
                 out["target"].extend(fs)
         return out
 
@@ -181,7 +189,9 @@ def main() -> None:
     ap.add_argument("--epochs", type=int, default=4)
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--tol", type=float, default=1e-3)
+    ap.add_argument("--tol", type=float, default=1e-3, help="stopping tolerance of the evaluation")
+    ap.add_argument("--target-tol", type=float, default=0.0,
+                    help="> 0: targets are TNLM runs to this tolerance (else K = 50)")
     ap.add_argument("--kmax", type=int, default=300)
     ap.add_argument("--base", type=int, default=32)
     ap.add_argument("--levels", type=int, default=4)
@@ -189,7 +199,7 @@ def main() -> None:
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     torch.cuda.set_device(0)
-    maker = PairMaker(torch, tn)
+    maker = PairMaker(torch, tn, k_outer=args.kmax if args.target_tol > 0 else 50, tol=args.target_tol)
     t0 = time.perf_counter()
     train = maker.make(list(range(args.seed, args.seed + args.train)), keep_all=False)
     test = maker.make(list(range(args.seed + 100000, args.seed + 100000 + args.test)))
@@ -234,7 +244,10 @@ def main() -> None:
     summ = {k: float(np.mean([r[k] for r in rows])) for k in
             ("iters_cold", "iters_warm", "ms_cold", "ms_warm", "err_truth_cold", "err_truth_warm",
              "warm_vs_cold")}
+    ti = train.get("target_iters", [])
     out = {"train": args.train, "test": args.test, "epochs": args.epochs, "batch": args.batch,
+           "target": (f"TNLM to tol {args.target_tol} (mean {np.mean(ti):.1f} iterations)" if ti
+                      else "TNLM after K = 50"),
            "net": {"base": args.base, "levels": args.levels, "params": net.param_count},
            "seconds": {"data": round(t_data, 1), "train": round(t_train, 1)},
            "loss": hist, "identity_test_loss": base_loss, "tol": args.tol,
