@@ -374,7 +374,7 @@ def run_batch(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    items = synth.batch_cases(args.batch_size)
+    items = synth.batch_cases(args.batch_size, precision=1 if args.precision == "mixed" else 0)
     geos, params, ys, ws, fs, f0s = [], [], [], [], [], []
     for c, off in items:
         d = synth.make_inputs(c, off)
@@ -427,12 +427,15 @@ def run_batch(args):
     out = {"metric": METRIC, "value": round(n * args.steps / (total_ms / 1e3), 4), "unit": UNIT,
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": round(total_ms / args.steps, 1), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if args.precision == "fp32" else "f32 (patch cross terms f16x2 on tensor cores)",
            "data": "synthetic (seeded ellipse phantom, analytic line integrals, Poisson noise)",
            "config": {"workload": (f"batch of {n} 10-phase slices per step, sides from 256/384/512 "
                                    "(384 mm field), 60/90/180/360 views, I0 log-uniform 5e3..1e6, "
-                                   "d=5, W=11, K=50, FBP start, tensor-core (split-FP16) patch "
-                                   "distances; one graph per outer iteration for all slices "
+                                   "d=5, W=11, K=50, FBP start, "
+                                   + ("tensor-core (split-FP16) patch distances" if args.precision == "mixed"
+                                      else "FP32 patch distances")
+                                   + "; one graph per outer iteration for all slices "
                                    "(tnlm_reconstruct_batch), launch shapes autotuned"),
                       "slices": sizes, "autotuned": {f"{k[0]}^2/{k[1]}v": v for k, v in tuned.items()},
                       "l2": "inputs far larger than L2", "parallelism": "batch x1"},
@@ -514,6 +517,8 @@ def main():
     ap.add_argument("--workload", choices=("slice", "batch"), default="slice",
                     help="slice: the three 256^2 scenarios (default line); batch: many uneven slices")
     ap.add_argument("--batch-size", type=int, default=64)
+    ap.add_argument("--precision", choices=("mixed", "fp32"), default="mixed",
+                    help="patch distances of the batch workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
