@@ -522,6 +522,7 @@ constexpr int kTmaConsumers = 256;
 constexpr int kTmaThreads = kTmaConsumers + 32;
 constexpr int kTmaStageFloats = kTmaTH * (kTmaTW + kTmaBW);   // 2112 floats = 66 x 128 B
 constexpr int kTmaStages = 4;
+constexpr int kTmaUBufs = 2;      // neighbour-iterate tile buffers (2: the next tile's loads overlap)
 // neighbour-phase tile: the 64 x 16 pixels widened by 8 columns and 7 rows
 // on each side (every window up to 15 x 15), loaded once per block
 constexpr int kTmaUW = kTmaTW + 16, kTmaUH = kTmaTH + 14;
@@ -556,7 +557,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
     // tensor-copy destinations must be 128-byte aligned: round the base up
     float* stages = (float*)(((uintptr_t)tma_sm_raw + 127) & ~(uintptr_t)127);
     float* utile = stages + kTmaStages * kTmaStageFloats;     // [2 buffers][2 phases][UH][UW]
-    uint64_t* full = (uint64_t*)(utile + 4 * kTmaUFloats);
+    uint64_t* full = (uint64_t*)(utile + 2 * kTmaUBufs * kTmaUFloats);
     uint64_t* empty = full + kTmaStages;
     uint64_t* ufull = empty + kTmaStages;                      // [2]
     uint64_t* uempty = ufull + 2;                              // [2]
@@ -593,12 +594,13 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
             int kk = 0, nu = 0;
             bool ok = true;
             for (int t = t0, u = 0; t < t1 && ok; t += tstep, ++u) {
-                const int ub = u & 1;
+                const int ub = u % kTmaUBufs;
                 const int tile = t / N, i = t % N;
                 const int X0 = (tile % tilesx) * kTmaTW, Y0 = (tile / tilesx) * kTmaTH;
                 const int ip = (i + N - 1) % N, inx = (i + 1) % N;
                 // iterate tiles of both neighbour phases (rows/columns outside the plane read 0)
-                if (u >= 2 && !mbar_wait_bounded(&uempty[ub], (unsigned)(((u - 2) >> 1) & 1))) {
+                if (u >= kTmaUBufs &&
+                    !mbar_wait_bounded(&uempty[ub], (unsigned)(((u - kTmaUBufs) / kTmaUBufs) & 1))) {
                     ok = false;
                     break;
                 }
@@ -641,7 +643,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
         bool bad = false, ok = true;
         int kk = 0;
         for (int t = t0, u = 0; t < t1 && ok; t += tstep, ++u) {
-            const int ub = u & 1;
+            const int ub = u % kTmaUBufs;
             const int tile = t / N, i = t % N;
             const int x0 = (tile % tilesx) * kTmaTW + 4 * tx, y = (tile / tilesx) * kTmaTH + ty;
             const bool rowin = x0 < nx && y < ny;
@@ -658,7 +660,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
             // window rows of this thread inside the neighbour tiles
             const float* Un = utile + ub * 2 * kTmaUFloats + (ty + 7) * kTmaUW + 4 * tx + 8 - UOFF;
             const float* Up = Un + kTmaUFloats;
-            if (!mbar_wait_bounded(&ufull[ub], (unsigned)((u >> 1) & 1))) {
+            if (!mbar_wait_bounded(&ufull[ub], (unsigned)((u / kTmaUBufs) & 1))) {
                 s_abort = 1;
                 ok = false;
                 break;
@@ -751,8 +753,8 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
             atomicOr(a.err, 16);
             // drain the block's copies in flight: the last use of each iterate
             // buffer and the last kTmaStages stage loads
-            for (int u = max(0, s_uissued - 2); u < s_uissued; ++u)
-                mbar_wait_bounded(&ufull[u & 1], (unsigned)((u >> 1) & 1));
+            for (int u = max(0, s_uissued - kTmaUBufs); u < s_uissued; ++u)
+                mbar_wait_bounded(&ufull[u % kTmaUBufs], (unsigned)((u / kTmaUBufs) & 1));
             for (int kk = s_issued - kTmaStages; kk < s_issued; ++kk)
                 if (kk >= 0) mbar_wait_bounded(&full[kk % kTmaStages], (unsigned)((kk / kTmaStages) & 1));
         }
@@ -771,7 +773,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
 }
 
 static size_t tma_smem() {
-    return 128 + sizeof(float) * (kTmaStages * kTmaStageFloats + 4 * kTmaUFloats) +
+    return 128 + sizeof(float) * (kTmaStages * kTmaStageFloats + 2 * kTmaUBufs * kTmaUFloats) +
            8 * (2 * kTmaStages + 4);
 }
 
