@@ -521,8 +521,8 @@ constexpr int kTmaBW = kTmaTW + 4;
 constexpr int kTmaConsumers = 256;
 constexpr int kTmaThreads = kTmaConsumers + 32;
 constexpr int kTmaStageFloats = kTmaTH * (kTmaTW + kTmaBW);   // 2112 floats = 66 x 128 B
-constexpr int kTmaStages = 4;
-constexpr int kTmaUBufs = 2;      // neighbour-iterate tile buffers (2: the next tile's loads overlap)
+constexpr int kTmaStages = 6;
+constexpr int kTmaUBufs = 1;      // neighbour-iterate tile buffers (2 lets a multi-tile CTA load the next tile early)
 // neighbour-phase tile: the 64 x 16 pixels widened by 8 columns and 7 rows
 // on each side (every window up to 15 x 15), loaded once per block
 constexpr int kTmaUW = kTmaTW + 16, kTmaUH = kTmaTH + 14;
