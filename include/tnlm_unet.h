@@ -16,7 +16,9 @@
  *
  * Numerics: the input, the weights seen by the convolutions and every
  * post-ReLU activation are stored in BF16 (round to nearest even); sums,
- * outputs, gradients, master weights and Adam moments are FP32.  Max pooling
+ * outputs, gradients, master weights and Adam moments are FP32.  Forward
+ * 3x3 layers with 32, 64, 128 or 256 output channels run on the tensor
+ * cores (tcgen05, BF16 x BF16 -> FP32); the rest on the CUDA cores.  Max pooling
  * sends its gradient to the first maximum of each 2x2 window (row-major).
  * Results are deterministic.
  *

@@ -18,6 +18,7 @@
 // pixels (weight and bias gradients, loss) are two-stage with a fixed
 // order, so a training step is deterministic.
 #include "internal.cuh"
+#include "tcgen05.cuh"
 #include "tnlm_unet.h"
 
 #include <cuda_bf16.h>
@@ -121,6 +122,145 @@ __global__ void __launch_bounds__(128) k_conv3(const TIN* __restrict__ in, long 
             else ((float*)out)[off] = v;
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// conv3x3 forward on the tensor cores (tcgen05): an implicit GEMM with
+// M = a 16 x 8 pixel tile (128 rows), N = COUT output channels, K = 9 taps x
+// Cin in steps of 16 channels; BF16 operands, FP32 accumulator in tensor
+// memory.  Per 16-channel chunk the 18 x 10 input halo is staged in shared
+// memory as [channel group of 8][row][col][8 channels], so the A operand of
+// a tap is one 16-byte copy per (pixel, channel group) into the canonical
+// K-major layout; B comes pre-packed in that layout (k_pack_tc).  The
+// operands are double-buffered: step s + 1 is built while the MMA of step s
+// runs; its completion (tcgen05.commit -> mbarrier) frees the buffer.  The
+// epilogue adds the bias, applies ReLU and stores BF16 (NCHW).
+// ---------------------------------------------------------------------------
+constexpr int kTcvTW = 16, kTcvTH = 8;
+constexpr int kTcvHW = kTcvTW + 2, kTcvHH = kTcvTH + 2;      // halo 18 x 10
+
+__device__ __forceinline__ int tc_off(int row, int k) {      // bytes; rows of 16 K-elements
+    return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(256) k_conv3_tc(const bf16* __restrict__ in, long in_bs, int Cin,
+                                                  const uint4* __restrict__ wpk, const float* __restrict__ bias,
+                                                  bf16* __restrict__ out, long out_bs, int H, int W,
+                                                  int tiles_x, int* err) {
+    __shared__ __align__(128) uint4 halo[2 * kTcvHH * kTcvHW];          // [cg][y][x] x 8 BF16
+    __shared__ __align__(1024) uint4 sA[2][128 * 2];                    // 2 buffers x 128 rows x 32 B
+    __shared__ __align__(1024) uint4 sB[2][COUT * 2];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int t = blockIdx.x, b = blockIdx.y;
+    const int X0 = (t % tiles_x) * kTcvTW, Y0 = (t / tiles_x) * kTcvTH;
+    const long plane = (long)H * W;
+    const bf16* inb = in + (long)b * in_bs;
+    if (warp == 0) {
+        tmem_alloc(&s_taddr, COUT < 32 ? 32 : COUT);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    const int nchunk = (Cin + 15) / 16;
+    constexpr uint32_t idesc = idesc_f16(128, COUT, true);
+    int s = 0;
+    bool ok = true;
+    for (int ch = 0; ch < nchunk && ok; ++ch) {
+        const int c0 = ch * 16;
+        __syncthreads();      // the previous chunk's A builds have read the halo
+        bf16* hb = (bf16*)halo;
+        for (int e = tid; e < 16 * kTcvHH * kTcvHW; e += 256) {
+            const int c = e / (kTcvHH * kTcvHW), pix = e % (kTcvHH * kTcvHW);
+            const int yy = Y0 - 1 + pix / kTcvHW, xx = X0 - 1 + pix % kTcvHW;
+            bf16 v = __float2bfloat16_rn(0.f);
+            if (c0 + c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                v = inb[(long)(c0 + c) * plane + (long)yy * W + xx];
+            hb[((c >> 3) * kTcvHH * kTcvHW + pix) * 8 + (c & 7)] = v;
+        }
+        __syncthreads();
+        for (int tap = 0; tap < 9; ++tap, ++s) {
+            const int buf = s & 1;
+            if (s >= 2 && !mbar_wait_bounded(&bar[buf], (unsigned)(((s - 2) >> 1) & 1))) {
+                s_abort = 1;
+                atomicOr(err, 16);
+            }
+            {   // A: pixel m = tid & 127, channel group tid >> 7
+                const int m = tid & 127, cg = tid >> 7;
+                const int y = (m >> 4) + tap / 3, x = (m & 15) + tap % 3;
+                sA[buf][tc_off(m, 8 * cg) >> 4] = halo[(cg * kTcvHH + y) * kTcvHW + x];
+            }
+            const uint4* wsrc = wpk + (long)(tap * nchunk + ch) * COUT * 2;
+            for (int q = tid; q < COUT * 2; q += 256) sB[buf][q] = wsrc[q];
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (s_abort) { ok = false; break; }
+            if (tid == 0) {
+                tc_fence_after();
+                umma_f16(taddr, smem_desc(smem_u32(&sA[buf][0]), 128, 256), smem_desc(smem_u32(&sB[buf][0]), 128, 256),
+                         idesc, s > 0 ? 1u : 0u);
+                umma_commit(&bar[buf]);
+            }
+        }
+    }
+    // s MMAs were issued; the last one's commit covers all earlier ones (also
+    // after an abort, before the tensor memory is released)
+    if (s > 0 && !mbar_wait_bounded(&bar[(s - 1) & 1], (unsigned)(((s - 1) >> 1) & 1))) {
+        atomicOr(err, 16);
+        ok = false;
+    }
+    tc_fence_after();
+    if (ok) {
+        // epilogue: warp w reads lanes 32 (w % 4) .. and half (w / 4) of the columns
+        const int q = warp & 3, half = warp >> 2;
+        const int m = 32 * q + lane;
+        const int y = Y0 + (m >> 4), x = X0 + (m & 15);
+        const bool pin = y < H && x < W;
+        constexpr int CH = COUT / 2;
+        for (int o0 = half * CH; o0 < (half + 1) * CH; o0 += 16) {
+            uint32_t v[16];
+            __syncwarp();
+            tmem_ld16(taddr + ((uint32_t)(32 * q) << 16) + (uint32_t)o0, v);
+            if (pin) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float r = fmaxf(__uint_as_float(v[j]) + bias[o0 + j], 0.f);
+                    out[(long)b * out_bs + (long)(o0 + j) * plane + (long)y * W + x] = __float2bfloat16_rn(r);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(taddr, COUT < 32 ? 32 : COUT);
+}
+
+// Packs the BF16 weights of a 3x3 layer for k_conv3_tc: for tap k and
+// channel chunk ch, the COUT x 16 block (output o, channel c0 + j) in the
+// canonical K-major layout; channels past Cin are zero.
+__global__ void k_pack_tc(const float* __restrict__ w, int O, int C, bf16* __restrict__ dst) {
+    const int nchunk = (C + 15) / 16;
+    const long n = (long)9 * nchunk * O * 16;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = (int)(i % 16), o = (int)((i / 16) % O);
+    const int ch = (int)((i / ((long)16 * O)) % nchunk), k = (int)(i / ((long)16 * O * nchunk));
+    const int c = ch * 16 + j;
+    const float v = c < C ? w[((long)o * C + c) * 9 + k] : 0.f;
+    dst[(long)(k * nchunk + ch) * O * 16 + tc_off(o, j) / 2] = __float2bfloat16_rn(v);
 }
 
 // ---------------------------------------------------------------------------
@@ -417,6 +557,9 @@ struct tnlm_unet {
     long nparam = 0;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;   // FP32 [nparam]
     tnlm::unet::bf16 *wb = nullptr, *wt = nullptr;                  // BF16 copies
+    tnlm::unet::bf16* wtc = nullptr;                                // tensor-core packing of 3x3 layers
+    std::vector<long> tcoff;                                        // per layer offset in wtc (-1: none)
+    int* derr = nullptr;                                            // device error flags
     long adam_t = 0;
     // activations (BF16) and gradient scratch (FP32), sized for cap_pixels * batch
     long cap = 0;
@@ -529,6 +672,27 @@ void conv3(const TIN* in, long in_bs, int Cin, const bf16* mask, long mask_bs, c
                                                  Cout, H, W);
 }
 
+// Forward 3x3 layer: the tensor-core kernel for 32/64/128/256 output
+// channels, the CUDA-core one otherwise.
+void conv3_fwd(tnlm_unet* n, int li, const bf16* in, long in_bs, int Cin, bf16* out, long out_bs, int Cout,
+               int H, int W, int B, cudaStream_t st) {
+    const Layer& Ly = n->layers[li];
+    const long to = n->tcoff[li];
+    if (to >= 0) {
+        const int tx = (W + kTcvTW - 1) / kTcvTW, ty = (H + kTcvTH - 1) / kTcvTH;
+        dim3 grid(tx * ty, B);
+        const uint4* wp = (const uint4*)(n->wtc + to);
+        switch (Cout) {
+            case 32: k_conv3_tc<32><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            case 64: k_conv3_tc<64><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            case 128: k_conv3_tc<128><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            case 256: k_conv3_tc<256><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            default: break;
+        }
+    }
+    conv3<bf16, true, true>(in, in_bs, Cin, nullptr, 0, n->wb + Ly.woff, n->w + Ly.boff, out, out_bs, Cout, H, W, B, st);
+}
+
 tnlm_status forward(tnlm_unet* n, const float* x, const Plan& P, cudaStream_t st) {
     const int L = P.L, B = P.B;
     const long n0 = (long)B * n->in_ch * P.H * P.W;
@@ -548,14 +712,10 @@ tnlm_status forward(tnlm_unet* n, const float* x, const Plan& P, cudaStream_t st
             k_pool<<<grid1(np), 256, 0, st>>>(ep, ebs, P.c[l - 1], H * 2, W * 2, B, P.ain[l]);
             in = P.ain[l]; in_bs = (long)P.c[l - 1] * P.hw[l]; cin = P.c[l - 1];
         }
-        const Layer& a = n->layers[li++];
-        const Layer& b = n->layers[li++];
-        conv3<bf16, true, true>(in, in_bs, cin, nullptr, 0, n->wb + a.woff, n->w + a.boff, P.e1[l],
-                                (long)P.c[l] * P.hw[l], P.c[l], H, W, B, st);
+        conv3_fwd(n, li++, in, in_bs, cin, P.e1[l], (long)P.c[l] * P.hw[l], P.c[l], H, W, B, st);
         long ebs;
         bf16* ep = e_ptr(P, l, &ebs);
-        conv3<bf16, true, true>(P.e1[l], (long)P.c[l] * P.hw[l], P.c[l], nullptr, 0, n->wb + b.woff,
-                                n->w + b.boff, ep, ebs, P.c[l], H, W, B, st);
+        conv3_fwd(n, li++, P.e1[l], (long)P.c[l] * P.hw[l], P.c[l], ep, ebs, P.c[l], H, W, B, st);
     }
     const bf16* d = P.eL[0];
     for (int l = L - 2; l >= 0; --l) {
@@ -563,12 +723,9 @@ tnlm_status forward(tnlm_unet* n, const float* x, const Plan& P, cudaStream_t st
         const long cbs = (long)(P.c[l + 1] + P.c[l]) * P.hw[l];
         const long nu = (long)B * P.c[l + 1] * P.hw[l];
         k_up<<<grid1(nu), 256, 0, st>>>(d, P.c[l + 1], H, W, B, P.cat[l], cbs);
-        const Layer& a = n->layers[li++];
-        const Layer& b = n->layers[li++];
-        conv3<bf16, true, true>(P.cat[l], cbs, P.c[l + 1] + P.c[l], nullptr, 0, n->wb + a.woff,
-                                n->w + a.boff, P.d1[l], (long)P.c[l] * P.hw[l], P.c[l], H, W, B, st);
-        conv3<bf16, true, true>(P.d1[l], (long)P.c[l] * P.hw[l], P.c[l], nullptr, 0, n->wb + b.woff,
-                                n->w + b.boff, P.d2[l], (long)P.c[l] * P.hw[l], P.c[l], H, W, B, st);
+        conv3_fwd(n, li++, P.cat[l], cbs, P.c[l + 1] + P.c[l], P.d1[l], (long)P.c[l] * P.hw[l], P.c[l], H, W, B, st);
+        conv3_fwd(n, li++, P.d1[l], (long)P.c[l] * P.hw[l], P.c[l], P.d2[l], (long)P.c[l] * P.hw[l], P.c[l], H, W,
+                  B, st);
         d = P.d2[l];
     }
     const Layer& f = n->layers[li];
@@ -702,10 +859,15 @@ tnlm_status backward(tnlm_unet* n, const Plan& P, const float* gout_final, cudaS
 }
 
 tnlm_status repack(tnlm_unet* n, cudaStream_t st) {
-    for (const Layer& Ly : n->layers) {
+    for (size_t i = 0; i < n->layers.size(); ++i) {
+        const Layer& Ly = n->layers[i];
         const long nw = (long)Ly.cout * Ly.cin * Ly.k * Ly.k;
         k_pack_w<<<grid1(nw), 256, 0, st>>>(n->w + Ly.woff, Ly.cout, Ly.cin, Ly.k * Ly.k, n->wb + Ly.woff,
                                             Ly.k == 3 ? n->wt + Ly.woff : nullptr);
+        if (n->tcoff[i] >= 0) {
+            const long np = 9L * ((Ly.cin + 15) / 16) * Ly.cout * 16;
+            k_pack_tc<<<grid1(np), 256, 0, st>>>(n->w + Ly.woff, Ly.cout, Ly.cin, n->wtc + n->tcoff[i]);
+        }
     }
     UCK(cudaGetLastError(), "weight packing");
     return TNLM_OK;
@@ -759,6 +921,21 @@ tnlm_status tnlm_unet_create(int in_ch, int out_ch, int base, int levels, int de
     }
     n->g = n->w + off; n->m = n->g + off; n->v = n->m + off;
     n->wt = n->wb + off;
+    long tco = 0;
+    for (const Layer& Ly : n->layers) {
+        const bool tc = Ly.k == 3 && (Ly.cout == 32 || Ly.cout == 64 || Ly.cout == 128 || Ly.cout == 256);
+        n->tcoff.push_back(tc ? tco : -1);
+        if (tc) tco += 9L * ((Ly.cin + 15) / 16) * Ly.cout * 16;
+    }
+    e = cudaMalloc(&n->wtc, sizeof(bf16) * (tco > 0 ? tco : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&n->derr, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(n->w); cudaFree(n->wb); cudaFree(n->wtc);
+        delete n;
+        return ufail(TNLM_ERR_OOM, "parameter buffers", e);
+    }
+    cudaMemset(n->wtc, 0, sizeof(bf16) * (tco > 0 ? tco : 1));
+    cudaMemset(n->derr, 0, sizeof(int));
     cudaMemset(n->w, 0, sizeof(float) * off * 4);
     cudaMemset(n->wb, 0, sizeof(bf16) * off * 2);
     *out = n;
@@ -769,7 +946,8 @@ void tnlm_unet_destroy(tnlm_unet* n) {
     if (!n) return;
     cudaSetDevice(n->device);
     cudaDeviceSynchronize();
-    cudaFree(n->w); cudaFree(n->wb); cudaFree(n->act); cudaFree(n->scratch); cudaFree(n->parts);
+    cudaFree(n->w); cudaFree(n->wb); cudaFree(n->wtc); cudaFree(n->derr); cudaFree(n->act);
+    cudaFree(n->scratch); cudaFree(n->parts);
     cudaFree(n->loss_part);
     delete n;
 }
@@ -843,6 +1021,12 @@ tnlm_status tnlm_unet_grads(tnlm_unet* n, const float* d_x, const float* d_targe
         double t = 0.0;
         for (double v : hp) t += v;
         *loss = t / (double)no;
+        int err = 0;
+        UCK(cudaMemcpy(&err, n->derr, sizeof(int), cudaMemcpyDeviceToHost), "error flags");
+        if (err) {
+            cudaMemset(n->derr, 0, sizeof(int));
+            return ufail(TNLM_ERR_TIMEOUT, "a tensor-core wait timed out");
+        }
     }
     return TNLM_OK;
 }
