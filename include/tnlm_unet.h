@@ -16,9 +16,13 @@
  *
  * Numerics: the input, the weights seen by the convolutions and every
  * post-ReLU activation are stored in BF16 (round to nearest even); sums,
- * outputs, gradients, master weights and Adam moments are FP32.  Forward
- * 3x3 layers with 32, 64, 128 or 256 output channels run on the tensor
- * cores (tcgen05, BF16 x BF16 -> FP32); the rest on the CUDA cores.  Max pooling
+ * outputs, gradients, master weights and Adam moments are FP32; a gradient
+ * entering a 3x3 convolution's input- and weight-gradient products is
+ * rounded to BF16 (the bias gradient uses it unrounded).  The 3x3 products
+ * run on the tensor cores (tcgen05, BF16 x BF16 -> FP32) where the channel
+ * counts allow (forward: 32/64/128/256 outputs; input gradient: 32/64/96/
+ * 128/192/256 inputs; weight gradient: width a multiple of 16), else on the
+ * CUDA cores with the same rounding.  Max pooling
  * sends its gradient to the first maximum of each 2x2 window (row-major).
  * Results are deterministic.
  *

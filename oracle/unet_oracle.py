@@ -15,9 +15,12 @@ Loss: mean squared error against the target.
 
 Storage emulation: the GPU keeps the input, the weights used in the
 convolutions and every post-ReLU activation in BF16 (round to nearest
-even), accumulates in FP32 and keeps gradients in FP32.  With bf16=True the
-oracle rounds the same values at the same points (and nothing else), so the
-two differ only by accumulation order.
+even), accumulates in FP32 and keeps gradients in FP32, except that a
+gradient entering a 3x3 convolution's backward products (input and weight
+gradients) is rounded to BF16 (the bias gradient and the final 1x1 layer
+use it unrounded).  With bf16=True the oracle rounds the same values at the
+same points (and nothing else), so the two differ only by accumulation
+order.
 
 Parameter order (flat list of (weight, bias)): encoder l = 0..L-1 conv a, b;
 decoder l = L-2..0 conv a, b; the final 1x1 convolution.  Weights are
@@ -161,6 +164,12 @@ def forward(params, x, levels, bf16_storage=True):
 def loss_and_grads(params, x, target, levels, bf16_storage=True):
     """MSE loss and its gradients w.r.t. every (weight, bias), FP64."""
     out, cache = forward(params, x, levels, bf16_storage)
+    q = bf16 if bf16_storage else (lambda a: a)
+
+    def conv3_bwd(xin, w, gz):
+        gx, gw, _ = conv3_backward(xin, w, q(gz))
+        return gx, gw, gz.sum(axis=(0, 2, 3))
+
     n = out.size
     loss = float(np.sum((out - target) ** 2) / n)
     g_out = 2.0 * (out - target) / n
@@ -177,9 +186,9 @@ def loss_and_grads(params, x, target, levels, bf16_storage=True):
     for l in range(0, levels - 1):
         c, a1, a2 = acts[levels + (levels - 2 - l)]
         g2 = g * (a2 > 0)
-        ga1, gw, gb = conv3_backward(a1, W[k][0], g2); grads[k] = (gw, gb); k -= 1
+        ga1, gw, gb = conv3_bwd(a1, W[k][0], g2); grads[k] = (gw, gb); k -= 1
         g1 = ga1 * (a1 > 0)
-        gc, gw, gb = conv3_backward(c, W[k][0], g1); grads[k] = (gw, gb); k -= 1
+        gc, gw, gb = conv3_bwd(c, W[k][0], g1); grads[k] = (gw, gb); k -= 1
         cu = acts[l + 1][2].shape[1]        # channels of the upsampled part (those of e_{l+1})
         g_up, g_skip = gc[:, :cu], gc[:, cu:]
         enc_grads[l] = g_skip
@@ -190,9 +199,9 @@ def loss_and_grads(params, x, target, levels, bf16_storage=True):
             g = g + enc_grads[l]
         a_in, a1, a2 = acts[l]
         g2 = g * (a2 > 0)
-        ga1, gw, gb = conv3_backward(a1, W[k][0], g2); grads[k] = (gw, gb); k -= 1
+        ga1, gw, gb = conv3_bwd(a1, W[k][0], g2); grads[k] = (gw, gb); k -= 1
         g1 = ga1 * (a1 > 0)
-        gin, gw, gb = conv3_backward(a_in, W[k][0], g1); grads[k] = (gw, gb); k -= 1
+        gin, gw, gb = conv3_bwd(a_in, W[k][0], g1); grads[k] = (gw, gb); k -= 1
         if l > 0:
             g = maxpool2_backward(acts[l - 1][2], gin)
     return loss, grads, out

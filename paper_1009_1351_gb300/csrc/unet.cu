@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(128) k_conv3(const TIN* __restrict__ in, long 
                 const long off = (long)(c0 + c) * plane + (long)yy * W + xx;
                 v = ld(inb + off);
                 if (mb && !(ld(mb + off) > 0.f)) v = 0.f;
+                if (sizeof(TIN) == 4) v = __bfloat162float(__float2bfloat16_rn(v));   // gradients enter as BF16
             }
             si[c][r / (kCT + 2)][r % (kCT + 2)] = v;
         }
@@ -143,11 +144,16 @@ __device__ __forceinline__ int tc_off(int row, int k) {      // bytes; rows of 1
     return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-template <int COUT>
-__global__ void __launch_bounds__(256) k_conv3_tc(const bf16* __restrict__ in, long in_bs, int Cin,
+// MODE 0: forward (BF16 input, + bias, ReLU, BF16 output).  MODE 1: input
+// gradient (FP32 gradient input times the ReLU mask of the layer, rounded to
+// BF16 on load; FP32 output, no bias).
+template <int COUT, int MODE>
+__global__ void __launch_bounds__(256) k_conv3_tc(const void* __restrict__ in_, long in_bs, int Cin,
+                                                  const bf16* __restrict__ mask, long mask_bs,
                                                   const uint4* __restrict__ wpk, const float* __restrict__ bias,
-                                                  bf16* __restrict__ out, long out_bs, int H, int W,
+                                                  void* __restrict__ out_, long out_bs, int H, int W,
                                                   int tiles_x, int* err) {
+    constexpr int TCOLS = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : (COUT <= 128 ? 128 : 256));
     __shared__ __align__(128) uint4 halo[2 * kTcvHH * kTcvHW];          // [cg][y][x] x 8 BF16
     __shared__ __align__(1024) uint4 sA[2][128 * 2];                    // 2 buffers x 128 rows x 32 B
     __shared__ __align__(1024) uint4 sB[2][COUT * 2];
@@ -158,9 +164,8 @@ __global__ void __launch_bounds__(256) k_conv3_tc(const bf16* __restrict__ in, l
     const int t = blockIdx.x, b = blockIdx.y;
     const int X0 = (t % tiles_x) * kTcvTW, Y0 = (t / tiles_x) * kTcvTH;
     const long plane = (long)H * W;
-    const bf16* inb = in + (long)b * in_bs;
     if (warp == 0) {
-        tmem_alloc(&s_taddr, COUT < 32 ? 32 : COUT);
+        tmem_alloc(&s_taddr, TCOLS);
         tmem_relinquish();
     }
     if (tid == 0) {
@@ -185,8 +190,16 @@ __global__ void __launch_bounds__(256) k_conv3_tc(const bf16* __restrict__ in, l
             const int c = e / (kTcvHH * kTcvHW), pix = e % (kTcvHH * kTcvHW);
             const int yy = Y0 - 1 + pix / kTcvHW, xx = X0 - 1 + pix % kTcvHW;
             bf16 v = __float2bfloat16_rn(0.f);
-            if (c0 + c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                v = inb[(long)(c0 + c) * plane + (long)yy * W + xx];
+            if (c0 + c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W) {
+                const long off = (long)(c0 + c) * plane + (long)yy * W + xx;
+                if (MODE == 0) {
+                    v = ((const bf16*)in_)[(long)b * in_bs + off];
+                } else {
+                    float g = ((const float*)in_)[(long)b * in_bs + off];
+                    if (mask && !(__bfloat162float(mask[(long)b * mask_bs + off]) > 0.f)) g = 0.f;
+                    v = __float2bfloat16_rn(g);
+                }
+            }
             hb[((c >> 3) * kTcvHH * kTcvHW + pix) * 8 + (c & 7)] = v;
         }
         __syncthreads();
@@ -236,8 +249,11 @@ __global__ void __launch_bounds__(256) k_conv3_tc(const bf16* __restrict__ in, l
             if (pin) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float r = fmaxf(__uint_as_float(v[j]) + bias[o0 + j], 0.f);
-                    out[(long)b * out_bs + (long)(o0 + j) * plane + (long)y * W + x] = __float2bfloat16_rn(r);
+                    const long off = (long)b * out_bs + (long)(o0 + j) * plane + (long)y * W + x;
+                    if (MODE == 0)
+                        ((bf16*)out_)[off] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[j]) + bias[o0 + j], 0.f));
+                    else
+                        ((float*)out_)[off] = __uint_as_float(v[j]);
                 }
             }
         }
@@ -245,7 +261,22 @@ __global__ void __launch_bounds__(256) k_conv3_tc(const bf16* __restrict__ in, l
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 0) tmem_dealloc(taddr, COUT < 32 ? 32 : COUT);
+    if (warp == 0) tmem_dealloc(taddr, TCOLS);
+}
+
+// Packs the transposed, flipped weights of a 3x3 layer for the input
+// gradient on k_conv3_tc: output channel n = the layer's input channel,
+// chunk channel j = the layer's output channel ch*16 + j, tap k -> 8 - k.
+__global__ void k_pack_tc_t(const float* __restrict__ w, int O, int C, bf16* __restrict__ dst) {
+    const int nchunk = (O + 15) / 16;
+    const long n = (long)9 * nchunk * C * 16;
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = (int)(i % 16), c = (int)((i / 16) % C);
+    const int ch = (int)((i / ((long)16 * C)) % nchunk), k = (int)(i / ((long)16 * C * nchunk));
+    const int o = ch * 16 + j;
+    const float v = o < O ? w[((long)o * C + c) * 9 + (8 - k)] : 0.f;
+    dst[(long)(k * nchunk + ch) * C * 16 + tc_off(c, j) / 2] = __float2bfloat16_rn(v);
 }
 
 // Packs the BF16 weights of a 3x3 layer for k_conv3_tc: for tap k and
@@ -261,6 +292,144 @@ __global__ void k_pack_tc(const float* __restrict__ w, int O, int C, bf16* __res
     const int c = ch * 16 + j;
     const float v = c < C ? w[((long)o * C + c) * 9 + k] : 0.f;
     dst[(long)(k * nchunk + ch) * O * 16 + tc_off(o, j) / 2] = __float2bfloat16_rn(v);
+}
+
+// ---------------------------------------------------------------------------
+// conv3x3 weight gradient on the tensor cores, first stage (split over
+// image rows):  D[o][c*9 + t] = sum_p gz[o][p] * in[c][p + off_t]  with
+// M = 128 output channels (zero rows past Cout), N = 16 input channels x 9
+// taps = 144, K = 16 consecutive pixels of one image row per MMA.  gz is the
+// FP32 gradient times the ReLU mask, rounded to BF16 (as everywhere a
+// gradient enters a convolution); in is the BF16 layer input.  Per step the
+// three input rows around the pixel row (16 channels x 18 pixels) are staged
+// in shared memory and the operands are built into double buffers in the
+// canonical K-major layout.  Needs W % 16 == 0.  The accumulator (144 of 256
+// TMEM columns) is written as this slice's partial sums [o][c][t].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_conv3_wgrad_tc(const float* __restrict__ gout, long g_bs,
+                                                        const bf16* __restrict__ act, long a_bs,
+                                                        const bf16* __restrict__ in, long in_bs, int Cin,
+                                                        int Cout, int H, int W, int B, int rows_per,
+                                                        float* __restrict__ part, int* err) {
+    __shared__ __align__(16) bf16 srow[16][3][20];                      // [c][row][x0-1 .. x0+16]
+    __shared__ __align__(1024) uint4 sA[2][128 * 2];
+    __shared__ __align__(1024) uint4 sB[2][144 * 2];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = blockIdx.x * 16, o0 = blockIdx.y * 128;
+    const long plane = (long)H * W;
+    const long r_begin = (long)blockIdx.z * rows_per, r_end = min((long)B * H, r_begin + rows_per);
+    if (warp == 0) {
+        tmem_alloc(&s_taddr, 256);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    constexpr uint32_t idesc = idesc_f16(128, 144, true);
+    int s = 0;
+    bool ok = true;
+    for (long br = r_begin; br < r_end && ok; ++br) {
+        const int b = (int)(br / H), y = (int)(br % H);
+        for (int x0 = 0; x0 < W && ok; x0 += 16, ++s) {
+            const int buf = s & 1;
+            if (s >= 2 && !mbar_wait_bounded(&bar[buf], (unsigned)(((s - 2) >> 1) & 1))) {
+                s_abort = 1;
+                atomicOr(err, 16);
+            }
+            // the three input rows of 16 channels, pixels x0-1 .. x0+16 (zero outside)
+            for (int e = tid; e < 16 * 3 * 18; e += 256) {
+                const int c = e / 54, r = (e / 18) % 3, xi = e % 18;
+                const int yy = y - 1 + r, xx = x0 - 1 + xi;
+                bf16 v = __float2bfloat16_rn(0.f);
+                if (c0 + c < Cin && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    v = in[(long)b * in_bs + (long)(c0 + c) * plane + (long)yy * W + xx];
+                srow[c][r][xi] = v;
+            }
+            {   // A: row o = tid & 127, pixels 8h .. 8h + 7 with h = tid >> 7
+                const int o = tid & 127, h = tid >> 7;
+                uint32_t pk[4] = {0u, 0u, 0u, 0u};
+                if (o0 + o < Cout) {
+                    const long off = (long)(o0 + o) * plane + (long)y * W + x0 + 8 * h;
+                    const float4 g0 = *(const float4*)(gout + (long)b * g_bs + off);
+                    const float4 g1 = *(const float4*)(gout + (long)b * g_bs + off + 4);
+                    float gv[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
+                    if (act) {
+                        const uint4 mr = *(const uint4*)(act + (long)b * a_bs + off);
+                        const bf16* mv = (const bf16*)&mr;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (!(__bfloat162float(mv[j]) > 0.f)) gv[j] = 0.f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        pk[j] = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(gv[2 * j])) |
+                                ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(gv[2 * j + 1])) << 16);
+                }
+                sA[buf][tc_off(o, 8 * h) >> 4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            __syncthreads();      // srow complete
+            for (int q = tid; q < 144 * 2; q += 256) {   // B: row n = c*9 + t, pixels 8h .. 8h + 7
+                const int n = q >> 1, h = q & 1, c = n / 9, t = n % 9;
+                const bf16* src = &srow[c][t / 3][8 * h + t % 3];
+                uint32_t pk[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    pk[j] = (uint32_t)__bfloat16_as_ushort(src[2 * j]) | ((uint32_t)__bfloat16_as_ushort(src[2 * j + 1]) << 16);
+                sB[buf][tc_off(n, 8 * h) >> 4] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            if (s_abort) { ok = false; break; }
+            if (tid == 0) {
+                tc_fence_after();
+                umma_f16(taddr, smem_desc(smem_u32(&sA[buf][0]), 128, 256), smem_desc(smem_u32(&sB[buf][0]), 128, 256),
+                         idesc, s > 0 ? 1u : 0u);
+                umma_commit(&bar[buf]);
+            }
+        }
+    }
+    if (s > 0 && !mbar_wait_bounded(&bar[(s - 1) & 1], (unsigned)(((s - 1) >> 1) & 1))) {
+        atomicOr(err, 16);
+        ok = false;
+    }
+    tc_fence_after();
+    if (ok && warp < 4) {
+        const int o = 32 * warp + lane;
+        for (int n0 = 0; n0 < 144; n0 += 16) {
+            uint32_t v[16];
+            __syncwarp();
+            if (s > 0) {
+                tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)n0, v);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = 0u;
+            }
+            if (o0 + o < Cout) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + j, c = n / 9, t = n % 9;
+                    if (c0 + c < Cin)
+                        part[((long)blockIdx.z * Cout * Cin + (long)(o0 + o) * Cin + c0 + c) * 9 + t] =
+                            __uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(taddr, 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -298,6 +467,7 @@ __global__ void __launch_bounds__(256) k_conv3_wgrad(const float* __restrict__ g
                     const long off = (long)(o0 + o) * plane + (long)y * W + x;
                     v = gout[(long)b * g_bs + off];
                     if (act && !(__bfloat162float(act[(long)b * a_bs + off]) > 0.f)) v = 0.f;
+                    v = __bfloat162float(__float2bfloat16_rn(v));   // gradients enter as BF16
                 }
                 sg[o][e % XT] = v;
             }
@@ -559,6 +729,8 @@ struct tnlm_unet {
     tnlm::unet::bf16 *wb = nullptr, *wt = nullptr;                  // BF16 copies
     tnlm::unet::bf16* wtc = nullptr;                                // tensor-core packing of 3x3 layers
     std::vector<long> tcoff;                                        // per layer offset in wtc (-1: none)
+    tnlm::unet::bf16* wtct = nullptr;                               // same for the input gradients
+    std::vector<long> tcofft;
     int* derr = nullptr;                                            // device error flags
     long adam_t = 0;
     // activations (BF16) and gradient scratch (FP32), sized for cap_pixels * batch
@@ -683,14 +855,36 @@ void conv3_fwd(tnlm_unet* n, int li, const bf16* in, long in_bs, int Cin, bf16* 
         dim3 grid(tx * ty, B);
         const uint4* wp = (const uint4*)(n->wtc + to);
         switch (Cout) {
-            case 32: k_conv3_tc<32><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
-            case 64: k_conv3_tc<64><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
-            case 128: k_conv3_tc<128><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
-            case 256: k_conv3_tc<256><<<grid, 256, 0, st>>>(in, in_bs, Cin, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            case 32: k_conv3_tc<32, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            case 64: k_conv3_tc<64, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            case 128: k_conv3_tc<128, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
+            case 256: k_conv3_tc<256, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
             default: break;
         }
     }
     conv3<bf16, true, true>(in, in_bs, Cin, nullptr, 0, n->wb + Ly.woff, n->w + Ly.boff, out, out_bs, Cout, H, W, B, st);
+}
+
+// Input gradient of 3x3 layer li: g (FP32, the layer's Cout channels, times
+// the mask) -> out (FP32, the layer's Cin channels).  Tensor cores when the
+// layer's Cin is 32/64/96/128/192/256, else the CUDA-core kernel.
+void conv3_dgrad(tnlm_unet* n, int li, const float* g, long g_bs, const bf16* mask, long m_bs, float* out,
+                 long out_bs, int H, int W, int B, cudaStream_t st) {
+    const Layer& Ly = n->layers[li];
+    const long to = n->tcofft[li];
+    if (to >= 0) {
+        const int tx = (W + kTcvTW - 1) / kTcvTW, ty = (H + kTcvTH - 1) / kTcvTH;
+        dim3 grid(tx * ty, B);
+        const uint4* wp = (const uint4*)(n->wtct + to);
+#define TNLM_DG(C) \
+    case C: k_conv3_tc<C, 1><<<grid, 256, 0, st>>>(g, g_bs, Ly.cout, mask, m_bs, wp, nullptr, out, out_bs, H, W, tx, n->derr); return;
+        switch (Ly.cin) {
+            TNLM_DG(32) TNLM_DG(64) TNLM_DG(96) TNLM_DG(128) TNLM_DG(192) TNLM_DG(256)
+            default: break;
+        }
+#undef TNLM_DG
+    }
+    conv3<float, false, false>(g, g_bs, Ly.cout, mask, m_bs, n->wt + Ly.woff, nullptr, out, out_bs, Ly.cin, H, W, B, st);
 }
 
 tnlm_status forward(tnlm_unet* n, const float* x, const Plan& P, cudaStream_t st) {
@@ -751,9 +945,15 @@ tnlm_status conv3_param_grads(tnlm_unet* n, const Layer& Ly, const float* gout, 
         UCK(cudaMalloc(&n->parts, sizeof(float) * S * nw), "gradient partials");
         n->part_cap = (long)S * nw;
     }
-    const int blocks = ((Ly.cout + 15) / 16) * ((Ly.cin + 15) / 16);
-    k_conv3_wgrad<TIN><<<dim3(blocks, S), 256, 0, st>>>(gout, g_bs, act, a_bs, in, in_bs, Ly.cin, Ly.cout,
-                                                        H, W, B, rows_per, n->parts);
+    if (sizeof(TIN) == 2 && W % 16 == 0) {
+        dim3 grid((Ly.cin + 15) / 16, (Ly.cout + 127) / 128, S);
+        k_conv3_wgrad_tc<<<grid, 256, 0, st>>>(gout, g_bs, act, a_bs, (const bf16*)in, in_bs, Ly.cin, Ly.cout, H,
+                                               W, B, rows_per, n->parts, n->derr);
+    } else {
+        const int blocks = ((Ly.cout + 15) / 16) * ((Ly.cin + 15) / 16);
+        k_conv3_wgrad<TIN><<<dim3(blocks, S), 256, 0, st>>>(gout, g_bs, act, a_bs, in, in_bs, Ly.cin, Ly.cout,
+                                                            H, W, B, rows_per, n->parts);
+    }
     k_reduce_parts<<<grid1(nw), 256, 0, st>>>(n->parts, S, nw, n->g + Ly.woff);
     k_bias_grad<<<Ly.cout, 256, 0, st>>>(gout, g_bs, act, a_bs, B, (long)H * W, n->g + Ly.boff);
     UCK(cudaGetLastError(), "gradient launch");
@@ -792,23 +992,22 @@ tnlm_status backward(tnlm_unet* n, const Plan& P, const float* gout_final, cudaS
         const int H = P.H >> l, W = P.W >> l;
         const long hw = P.hw[l];
         const int cl = P.c[l], cu = P.c[l + 1];
-        const Layer& b = n->layers[li--];
-        const Layer& a = n->layers[li--];
+        const int ib = li--, ia = li--;
+        const Layer& b = n->layers[ib];
+        const Layer& a = n->layers[ia];
         // conv b: input d1, output d2 (mask d2)
         tnlm_status s = conv3_param_grads<bf16>(n, b, g, (long)cl * hw, P.d2[l], (long)cl * hw, P.d1[l],
                                                 (long)cl * hw, H, W, B, st);
         if (s != TNLM_OK) return s;
         float* gd1 = (g == S0) ? S2 : S0;
-        conv3<float, false, false>(g, (long)cl * hw, cl, P.d2[l], (long)cl * hw, n->wt + b.woff, nullptr, gd1,
-                                   (long)cl * hw, cl, H, W, B, st);
+        conv3_dgrad(n, ib, g, (long)cl * hw, P.d2[l], (long)cl * hw, gd1, (long)cl * hw, H, W, B, st);
         // conv a: input concat, output d1 (mask d1)
         s = conv3_param_grads<bf16>(n, a, gd1, (long)cl * hw, P.d1[l], (long)cl * hw, P.cat[l],
                                     (long)(cu + cl) * hw, H, W, B, st);
         if (s != TNLM_OK) return s;
         float* gc = (l == 0) ? S1 : carve;
         const long gcbs = (long)(cu + cl) * hw;
-        conv3<float, false, false>(gd1, (long)cl * hw, cl, P.d1[l], (long)cl * hw, n->wt + a.woff, nullptr, gc,
-                                   gcbs, cu + cl, H, W, B, st);
+        conv3_dgrad(n, ia, gd1, (long)cl * hw, P.d1[l], (long)cl * hw, gc, gcbs, H, W, B, st);
         skipg[l] = gc + (long)cu * hw;
         skipbs[l] = gcbs;
         if (l > 0) carve += (long)B * (cu + cl) * hw;
@@ -824,8 +1023,9 @@ tnlm_status backward(tnlm_unet* n, const Plan& P, const float* gout_final, cudaS
         const int H = P.H >> l, W = P.W >> l;
         const long hw = P.hw[l];
         const int cl = P.c[l];
-        const Layer& b = n->layers[li--];
-        const Layer& a = n->layers[li--];
+        const int ib = li--, ia = li--;
+        const Layer& b = n->layers[ib];
+        const Layer& a = n->layers[ia];
         long ebs;
         const bf16* ep = e_ptr(P, l, &ebs);
         // conv b: input e1, output e (mask e)
@@ -833,8 +1033,7 @@ tnlm_status backward(tnlm_unet* n, const Plan& P, const float* gout_final, cudaS
                                                 B, st);
         if (s != TNLM_OK) return s;
         float* ge1 = (g == S0) ? S2 : S0;
-        conv3<float, false, false>(g, (long)cl * hw, cl, ep, ebs, n->wt + b.woff, nullptr, ge1,
-                                   (long)cl * hw, cl, H, W, B, st);
+        conv3_dgrad(n, ib, g, (long)cl * hw, ep, ebs, ge1, (long)cl * hw, H, W, B, st);
         // conv a: input x (level 0) or pooled e_{l-1}, output e1 (mask e1)
         const bf16* in = l == 0 ? P.xq : P.ain[l];
         const int cin = l == 0 ? n->in_ch : P.c[l - 1];
@@ -843,8 +1042,7 @@ tnlm_status backward(tnlm_unet* n, const Plan& P, const float* gout_final, cudaS
         if (s != TNLM_OK) return s;
         if (l == 0) break;
         float* gin = (ge1 == S0) ? S2 : S0;
-        conv3<float, false, false>(ge1, (long)cl * hw, cl, P.e1[l], (long)cl * hw, n->wt + a.woff, nullptr, gin,
-                                   (long)cin * hw, cin, H, W, B, st);
+        conv3_dgrad(n, ia, ge1, (long)cl * hw, P.e1[l], (long)cl * hw, gin, (long)cin * hw, H, W, B, st);
         // gradient of e_{l-1}: pool^T(gin) + its skip gradient
         long pbs;
         const bf16* pe = e_ptr(P, l - 1, &pbs);
@@ -867,6 +1065,10 @@ tnlm_status repack(tnlm_unet* n, cudaStream_t st) {
         if (n->tcoff[i] >= 0) {
             const long np = 9L * ((Ly.cin + 15) / 16) * Ly.cout * 16;
             k_pack_tc<<<grid1(np), 256, 0, st>>>(n->w + Ly.woff, Ly.cout, Ly.cin, n->wtc + n->tcoff[i]);
+        }
+        if (n->tcofft[i] >= 0) {
+            const long np = 9L * ((Ly.cout + 15) / 16) * Ly.cin * 16;
+            k_pack_tc_t<<<grid1(np), 256, 0, st>>>(n->w + Ly.woff, Ly.cout, Ly.cin, n->wtct + n->tcofft[i]);
         }
     }
     UCK(cudaGetLastError(), "weight packing");
@@ -921,20 +1123,26 @@ tnlm_status tnlm_unet_create(int in_ch, int out_ch, int base, int levels, int de
     }
     n->g = n->w + off; n->m = n->g + off; n->v = n->m + off;
     n->wt = n->wb + off;
-    long tco = 0;
+    long tco = 0, tcot = 0;
     for (const Layer& Ly : n->layers) {
         const bool tc = Ly.k == 3 && (Ly.cout == 32 || Ly.cout == 64 || Ly.cout == 128 || Ly.cout == 256);
         n->tcoff.push_back(tc ? tco : -1);
         if (tc) tco += 9L * ((Ly.cin + 15) / 16) * Ly.cout * 16;
+        const bool tt = Ly.k == 3 && (Ly.cin == 32 || Ly.cin == 64 || Ly.cin == 96 || Ly.cin == 128 ||
+                                      Ly.cin == 192 || Ly.cin == 256);
+        n->tcofft.push_back(tt ? tcot : -1);
+        if (tt) tcot += 9L * ((Ly.cout + 15) / 16) * Ly.cin * 16;
     }
     e = cudaMalloc(&n->wtc, sizeof(bf16) * (tco > 0 ? tco : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&n->wtct, sizeof(bf16) * (tcot > 0 ? tcot : 1));
     if (e == cudaSuccess) e = cudaMalloc(&n->derr, sizeof(int));
     if (e != cudaSuccess) {
-        cudaFree(n->w); cudaFree(n->wb); cudaFree(n->wtc);
+        cudaFree(n->w); cudaFree(n->wb); cudaFree(n->wtc); cudaFree(n->wtct);
         delete n;
         return ufail(TNLM_ERR_OOM, "parameter buffers", e);
     }
     cudaMemset(n->wtc, 0, sizeof(bf16) * (tco > 0 ? tco : 1));
+    cudaMemset(n->wtct, 0, sizeof(bf16) * (tcot > 0 ? tcot : 1));
     cudaMemset(n->derr, 0, sizeof(int));
     cudaMemset(n->w, 0, sizeof(float) * off * 4);
     cudaMemset(n->wb, 0, sizeof(bf16) * off * 2);
@@ -946,7 +1154,7 @@ void tnlm_unet_destroy(tnlm_unet* n) {
     if (!n) return;
     cudaSetDevice(n->device);
     cudaDeviceSynchronize();
-    cudaFree(n->w); cudaFree(n->wb); cudaFree(n->wtc); cudaFree(n->derr); cudaFree(n->act);
+    cudaFree(n->w); cudaFree(n->wb); cudaFree(n->wtc); cudaFree(n->wtct); cudaFree(n->derr); cudaFree(n->act);
     cudaFree(n->scratch); cudaFree(n->parts);
     cudaFree(n->loss_part);
     delete n;
