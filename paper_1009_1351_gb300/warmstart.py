@@ -7,6 +7,7 @@ runs from it to the same stopping tolerance as from the usual start (the
 FBP of all views, box step 1) and decides the result.
 
     python -m paper_1009_1351_gb300.warmstart --train 4000 --test 200 --epochs 4
+    python -m paper_1009_1351_gb300.warmstart --time-net        (network timing only)
 
 1. Data: the plain method makes its own training pairs on the GPU.  Each
    seeded slice is a phantom of the ellipse family (256 x 256 at 1.5 mm,
@@ -179,11 +180,39 @@ def evaluate(torch, tn, net, maker: PairMaker, data, tol: float, kmax: int):
     return rows
 
 
+def time_net(torch, tn, base: int, levels: int, batch: int, reps: int = 10) -> Dict[str, float]:
+    """Device time of the network's forward pass and of one training step
+    (gradients + Adam) on random 10-phase 256 x 256 inputs."""
+    net = tn.UNet(10, 10, base, levels)
+    net.set_params(init_params(10, 10, base, levels, 1))
+    g = torch.Generator(device="cuda").manual_seed(1)
+    x = torch.rand((batch, 10, 256, 256), device="cuda", generator=g)
+    t = torch.rand_like(x)
+    o = torch.empty_like(x)
+    for _ in range(2):
+        net.forward(x, o)
+        net.grads(x, t)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e[0].record()
+    for _ in range(reps):
+        net.forward(x, o)
+    e[1].record()
+    for _ in range(reps):
+        net.grads(x, t)
+        net.adam_step(1e-3)
+    e[2].record()
+    torch.cuda.synchronize()
+    return {"batch": batch, "forward_ms": e[0].elapsed_time(e[1]) / reps,
+            "train_step_ms": e[1].elapsed_time(e[2]) / reps}
+
+
 def main() -> None:
     import torch
     import paper_1009_1351_gb300 as tn
 
     ap = argparse.ArgumentParser()
+    ap.add_argument("--time-net", action="store_true", help="only time the network (random data)")
     ap.add_argument("--train", type=int, default=4000)
     ap.add_argument("--test", type=int, default=200)
     ap.add_argument("--epochs", type=int, default=4)
@@ -199,6 +228,9 @@ def main() -> None:
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     torch.cuda.set_device(0)
+    if args.time_net:
+        print(json.dumps(time_net(torch, tn, args.base, args.levels, args.batch)))
+        return
     maker = PairMaker(torch, tn, k_outer=args.kmax if args.target_tol > 0 else 50, tol=args.target_tol)
     t0 = time.perf_counter()
     train = maker.make(list(range(args.seed, args.seed + args.train)), keep_all=False)
