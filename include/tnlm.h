@@ -230,9 +230,12 @@ tnlm_status tnlm_autotune(tnlm_geometry* geom, const tnlm_params* params, const 
  * slice runs exactly params[i].k_outer outer iterations of the algorithm box
  * (tol must be 0) from d_f[i], as tnlm_reconstruct would, with bitwise the
  * same result.  One outer iteration of all slices is captured as one CUDA
- * graph with a branch per slice and replayed once per iteration on the
- * stream, so kernels of different slices overlap; slices that reach their
- * k_outer leave the graph.  autotune_shapes != 0 runs tnlm_autotune first
+ * graph with a branch per slice, so kernels of different slices overlap.
+ * When every slice has the same k_outer the whole run is ONE graph launch:
+ * a conditional WHILE node around that iteration, counted down on the
+ * device; otherwise (or if the runtime refuses the loop graph) the
+ * iteration graph is replayed once per outer iteration and slices that
+ * reach their k_outer leave it.  autotune_shapes != 0 runs tnlm_autotune first
  * on every handle not yet tuned.  reports (may be NULL) is an array of
  * count reports.  Synchronises the stream.  Errors: as tnlm_reconstruct; the
  * first failing slice's status is returned after all reports are filled. */
@@ -240,6 +243,10 @@ tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_param
                                    int count, const float* const* d_y, const float* const* d_winv,
                                    float* const* d_f, tnlm_report* reports, int autotune_shapes,
                                    void* stream);
+
+/* 1 if the last tnlm_reconstruct_batch call on this host thread ran as a
+ * single loop-graph launch, else 0. */
+int tnlm_batch_last_was_loop(void);
 
 /* Kernel classes, for launch counting and optional device timing. */
 enum {

@@ -30,7 +30,7 @@ EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tn
             "tnlm_weights_size", "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct",
             "tnlm_last_error", "tnlm_debug_fail_alloc_after", "tnlm_profile_enable",
             "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp", "tnlm_autotune",
-            "tnlm_reconstruct_batch", "tnlm_fbp_phases", "tnlm_unet_create", "tnlm_unet_destroy", "tnlm_unet_param_count",
+            "tnlm_reconstruct_batch", "tnlm_batch_last_was_loop", "tnlm_fbp_phases", "tnlm_unet_create", "tnlm_unet_destroy", "tnlm_unet_param_count",
             "tnlm_unet_set_params", "tnlm_unet_get_params", "tnlm_unet_forward", "tnlm_unet_grads",
             "tnlm_unet_adam_step", "tnlm_unet_last_error")
 KCLASSES = ("prep", "project", "backproject", "cgls", "weights", "gj")
@@ -110,6 +110,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, vp]
     lib.tnlm_unet_last_error.restype = ctypes.c_char_p
+    lib.tnlm_batch_last_was_loop.restype = ctypes.c_int
     lib.tnlm_last_error.restype = ctypes.c_char_p
     lib.tnlm_debug_fail_alloc_after.argtypes = [ctypes.c_int]
     lib.tnlm_debug_fail_alloc_after.restype = None
@@ -317,6 +318,11 @@ def tnlm_reconstruct_batch(geoms, params, ys, winvs, fs, autotune: bool = True,
                     "data_residual": reps[k].data_residual,
                     "rel_change_hist": list(hist[k][0][:m]), "residual_hist": list(hist[k][1][:m])})
     return out
+
+
+def tnlm_batch_last_was_loop() -> bool:
+    """Whether the last batched call on this thread ran as one loop-graph launch."""
+    return bool(load_library().tnlm_batch_last_was_loop())
 
 
 def tnlm_debug_fail_alloc_after(n: int) -> None:

@@ -506,6 +506,15 @@ tnlm_status autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y, c
 // iteration, so kernels of different slices run side by side.  When slices
 // with fewer iterations finish, the graph is re-captured without them.
 // ---------------------------------------------------------------------------
+// Device-side loop of the batched graph: the body ends with a tick that
+// counts the outer iterations down and keeps the WHILE node running until
+// the count reaches zero.
+__global__ void k_loop_set(int* counter, int k) { *counter = k; }
+__global__ void k_loop_tick(cudaGraphConditionalHandle h, int* counter) {
+    const int c = --(*counter);
+    cudaGraphSetConditional(h, c > 0 ? 1u : 0u);
+}
+
 struct BatchItem {
     unsigned long long uid;
     unsigned tune_gen;
@@ -526,34 +535,22 @@ struct BatchState {
     cudaGraphExec_t exec = nullptr;
     std::vector<BatchItem> key;
     std::vector<std::array<long long, TNLM_KCLASS_COUNT>> launches;   // per slice and replay
+    // the whole K-iteration run as one launch: a WHILE node around the body
+    cudaGraphExec_t loop_exec = nullptr;
+    std::vector<BatchItem> loop_key;
+    bool loop_broken = false;          // the runtime refused the loop graph once: use replays
+    int* counter = nullptr;
+    std::vector<std::array<long long, TNLM_KCLASS_COUNT>> loop_launches;   // per slice and iteration
 };
 std::mutex g_batch_mu;
 std::map<int, BatchState*> g_batch;   // per device
+thread_local int g_last_batch_loop = 0;
 
-tnlm_status batch_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
-                        const std::vector<const tnlm_params*>& ps, const std::vector<const float*>& ys,
-                        const std::vector<float*>& fs) {
-    std::vector<BatchItem> key(gs.size());
-    for (size_t j = 0; j < gs.size(); ++j)
-        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws.base, ys[j], fs[j], *ps[j]};
-    if (B->exec && key == B->key) return TNLM_OK;
-    if (B->exec) {
-        cudaGraphExecDestroy(B->exec);
-        B->exec = nullptr;
-    }
-    if (!B->cap) CK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "capture stream");
-    while (B->streams.size() < gs.size()) {
-        cudaStream_t t;
-        CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "batch stream");
-        B->streams.push_back(t);
-    }
-    while (B->events.size() < gs.size() + 1) {
-        cudaEvent_t ev;
-        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
-        B->events.push_back(ev);
-    }
-    B->launches.assign(gs.size(), {});
-    CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+// Captures one outer iteration of every slice on the capture stream (which
+// is already capturing) as a fork/join of per-slice branches.
+tnlm_status capture_body(BatchState* B, const std::vector<tnlm_geometry*>& gs,
+                         const std::vector<const tnlm_params*>& ps, const std::vector<const float*>& ys,
+                         const std::vector<float*>& fs, cudaError_t* ce) {
     tnlm_status s = TNLM_OK;
     cudaError_t e = cudaEventRecord(B->events[0], B->cap);
     for (size_t j = 0; j < gs.size() && s == TNLM_OK && e == cudaSuccess; ++j) {
@@ -574,6 +571,119 @@ tnlm_status batch_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
         e = cudaEventRecord(B->events[j + 1], B->streams[j]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(B->cap, B->events[j + 1], 0);
     }
+    *ce = e;
+    return s;
+}
+
+tnlm_status batch_resources(BatchState* B, size_t n) {
+    if (!B->cap) CK(cudaStreamCreateWithFlags(&B->cap, cudaStreamNonBlocking), "capture stream");
+    while (B->streams.size() < n) {
+        cudaStream_t t;
+        CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking), "batch stream");
+        B->streams.push_back(t);
+    }
+    while (B->events.size() < n + 1) {
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
+        B->events.push_back(ev);
+    }
+    if (!B->counter) {
+        void* p = nullptr;
+        CK(dev_alloc(&p, sizeof(int)), "loop counter");
+        B->counter = (int*)p;
+    }
+    B->launches.assign(n, {});
+    return TNLM_OK;
+}
+
+// All K outer iterations of all slices as ONE graph launch: a conditional
+// WHILE node whose body is one outer iteration of every slice plus a tick
+// kernel that counts down.  Returns TNLM_OK with *built = false when the
+// runtime does not accept the loop graph (the caller then replays the
+// single-iteration graph K times).
+tnlm_status loop_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
+                       const std::vector<const tnlm_params*>& ps, const std::vector<const float*>& ys,
+                       const std::vector<float*>& fs, bool* built) {
+    *built = false;
+    if (B->loop_broken) return TNLM_OK;
+    std::vector<BatchItem> key(gs.size());
+    for (size_t j = 0; j < gs.size(); ++j)
+        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws.base, ys[j], fs[j], *ps[j]};
+    if (B->loop_exec && key == B->loop_key) {
+        *built = true;
+        return TNLM_OK;
+    }
+    if (B->loop_exec) {
+        cudaGraphExecDestroy(B->loop_exec);
+        B->loop_exec = nullptr;
+    }
+    tnlm_status s = batch_resources(B, gs.size());
+    if (s != TNLM_OK) return s;
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle h;
+    cudaGraphNodeParams np = {};
+    cudaGraphNode_t node;
+    cudaError_t e = cudaGraphCreate(&graph, 0);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) {
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    }
+    if (e == cudaSuccess)
+        e = cudaStreamBeginCaptureToGraph(B->cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        B->loop_broken = true;
+        return TNLM_OK;
+    }
+    cudaError_t ce = cudaSuccess;
+    s = capture_body(B, gs, ps, ys, fs, &ce);
+    if (s == TNLM_OK && ce == cudaSuccess) {
+        k_loop_tick<<<1, 1, 0, B->cap>>>(h, B->counter);
+        ce = cudaGetLastError();
+    }
+    cudaGraph_t body_out = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(B->cap, &body_out);
+    if (s != TNLM_OK) {
+        cudaGraphDestroy(graph);
+        return s;
+    }
+    if (ce == cudaSuccess && ee == cudaSuccess) ce = cudaGraphInstantiate(&B->loop_exec, graph, 0);
+    else if (ce == cudaSuccess) ce = ee;
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        B->loop_exec = nullptr;
+        B->loop_broken = true;
+        return TNLM_OK;
+    }
+    B->loop_key = key;
+    B->loop_launches = B->launches;
+    *built = true;
+    return TNLM_OK;
+}
+
+tnlm_status batch_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
+                        const std::vector<const tnlm_params*>& ps, const std::vector<const float*>& ys,
+                        const std::vector<float*>& fs) {
+    std::vector<BatchItem> key(gs.size());
+    for (size_t j = 0; j < gs.size(); ++j)
+        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws.base, ys[j], fs[j], *ps[j]};
+    if (B->exec && key == B->key) return TNLM_OK;
+    if (B->exec) {
+        cudaGraphExecDestroy(B->exec);
+        B->exec = nullptr;
+    }
+    tnlm_status s = batch_resources(B, gs.size());
+    if (s != TNLM_OK) return s;
+    CK(cudaStreamBeginCapture(B->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = cudaSuccess;
+    s = capture_body(B, gs, ps, ys, fs, &e);
     cudaGraph_t graph = nullptr;
     const cudaError_t ee = cudaStreamEndCapture(B->cap, &graph);
     if (s != TNLM_OK || e != cudaSuccess || ee != cudaSuccess) {
@@ -1017,6 +1127,8 @@ tnlm_status tnlm_autotune(tnlm_geometry* g, const tnlm_params* p, const float* d
     return TNLM_OK;
 }
 
+int tnlm_batch_last_was_loop(void) { return g_last_batch_loop; }
+
 tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_params* params,
                                    int count, const float* const* d_y, const float* const* d_winv,
                                    float* const* d_f, tnlm_report* reports, int autotune_shapes,
@@ -1064,6 +1176,26 @@ tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_param
         std::vector<const tnlm_params*> ps;
         std::vector<const float*> ys;
         std::vector<float*> fs;
+        g_last_batch_loop = 0;
+        bool same_k = kmax > 0;
+        for (int i = 0; i < count; ++i) same_k = same_k && params[i].k_outer == kmax;
+        if (same_k) {
+            for (int i = 0; i < count; ++i) {
+                gs.push_back(geoms[i]); ps.push_back(&params[i]); ys.push_back(d_y[i]); fs.push_back(d_f[i]);
+            }
+            bool built = false;
+            tnlm_status s = loop_graph(B, gs, ps, ys, fs, &built);
+            if (s != TNLM_OK) return s;
+            if (built) {
+                k_loop_set<<<1, 1, 0, st>>>(B->counter, kmax);
+                CK(cudaGetLastError(), "loop counter");
+                CK(cudaGraphLaunch(B->loop_exec, st), "batch loop graph launch");
+                for (size_t j = 0; j < gs.size(); ++j)
+                    for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) gs[j]->launches[c] += kmax * B->loop_launches[j][c];
+                kmax = 0;     // done: skip the per-iteration replays below
+                g_last_batch_loop = 1;
+            }
+        }
         for (int k = 0; k < kmax; ++k) {
             gs.clear(); ps.clear(); ys.clear(); fs.clear();
             for (int i = 0; i < count; ++i)

@@ -66,6 +66,7 @@ def test_batch_matches_single_calls_bitwise(tn):
         fs.append(dev(f0))
     reps = tn.tnlm_reconstruct_batch(geoms, [c.params for c in cases], ys, ws, fs, autotune=False)
     torch.cuda.synchronize()
+    assert not tn.tnlm_batch_last_was_loop()          # uneven K: per-iteration replays
     for c, f, (fr, rr), r in zip(cases, fs, ref, reps):
         assert torch.equal(f, fr), c.name
         assert r["iterations"] == c.params.k_outer
@@ -78,6 +79,31 @@ def test_batch_matches_single_calls_bitwise(tn):
         f1 = f.clone()
         tn.tnlm_reconstruct(g, c.params, y, w, f1)
         assert torch.equal(f1, f2), c.name
+
+
+def test_equal_k_batch_runs_as_one_loop_graph_and_matches_single_calls(tn):
+    """With one K for every slice the whole run is one graph launch (a
+    device-side WHILE loop around one outer iteration of all slices); the
+    results are still bitwise those of separate calls."""
+    cases = [synth.Case(c.name, c.geom, synth.Params(**{**c.params.__dict__, "k_outer": 3}), c.i0, c.seed,
+                        c.with_spine_diaphragm) for c in small_slices()]
+    geoms, ys, ws, fs, ref = [], [], [], [], []
+    for c in cases:
+        d, f0 = inputs(c)
+        g = tn.tnlm_create_geometry(c.geom)
+        f = dev(f0)
+        tn.tnlm_reconstruct(g, c.params, dev(d["y"]), dev(d["w"]), f)
+        ref.append(f)
+        geoms.append(tn.tnlm_create_geometry(c.geom))
+        ys.append(dev(d["y"])); ws.append(dev(d["w"])); fs.append(dev(f0))
+    for rep in range(2):      # the second call replays the cached loop graph
+        fr = [f.clone() for f in fs]
+        reps = tn.tnlm_reconstruct_batch(geoms, [c.params for c in cases], ys, ws, fr, autotune=False)
+        torch.cuda.synchronize()
+        assert tn.tnlm_batch_last_was_loop()
+        for c, f, r, rp in zip(cases, fr, ref, reps):
+            assert torch.equal(f, r), (rep, c.name)
+            assert rp["iterations"] == 3
 
 
 def test_batch_slice_matches_oracle(tn, oracle_mod):
