@@ -147,16 +147,19 @@ __device__ __forceinline__ int tc_off(int row, int k) {      // bytes; rows of 1
 // MODE 0: forward (BF16 input, + bias, ReLU, BF16 output).  MODE 1: input
 // gradient (FP32 gradient input times the ReLU mask of the layer, rounded to
 // BF16 on load; FP32 output, no bias).
+// A CTA computes output channels blockIdx.z * COUT .. + COUT - 1 of
+// cout_total (the N dimension is split over CTAs for the small deep levels).
 template <int COUT, int MODE>
 __global__ void __launch_bounds__(256) k_conv3_tc(const void* __restrict__ in_, long in_bs, int Cin,
                                                   const bf16* __restrict__ mask, long mask_bs,
                                                   const uint4* __restrict__ wpk, const float* __restrict__ bias,
                                                   void* __restrict__ out_, long out_bs, int H, int W,
-                                                  int tiles_x, int* err) {
+                                                  int tiles_x, int cout_total, int* err) {
     constexpr int TCOLS = COUT <= 32 ? 32 : (COUT <= 64 ? 64 : (COUT <= 128 ? 128 : 256));
+    const int oc0 = blockIdx.z * COUT;
     __shared__ __align__(128) uint4 halo[2 * kTcvHH * kTcvHW];          // [cg][y][x] x 8 BF16
-    __shared__ __align__(1024) uint4 sA[2][128 * 2];                    // 2 buffers x 128 rows x 32 B
-    __shared__ __align__(1024) uint4 sB[2][COUT * 2];
+    __shared__ __align__(1024) uint4 sA[2][3][128 * 2];                 // 2 buffers x 3 taps x 128 rows x 32 B
+    __shared__ __align__(1024) uint4 sB[2][3][COUT * 2];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t s_taddr;
     __shared__ int s_abort;
@@ -203,27 +206,35 @@ __global__ void __launch_bounds__(256) k_conv3_tc(const void* __restrict__ in_, 
             hb[((c >> 3) * kTcvHH * kTcvHW + pix) * 8 + (c & 7)] = v;
         }
         __syncthreads();
-        for (int tap = 0; tap < 9; ++tap, ++s) {
+        // one step = one kernel row (3 taps): three MMAs per barrier
+        for (int dy = 0; dy < 3; ++dy, ++s) {
             const int buf = s & 1;
             if (s >= 2 && !mbar_wait_bounded(&bar[buf], (unsigned)(((s - 2) >> 1) & 1))) {
                 s_abort = 1;
                 atomicOr(err, 16);
             }
-            {   // A: pixel m = tid & 127, channel group tid >> 7
+            {   // A: pixel m = tid & 127, channel group tid >> 7, the three taps of row dy
                 const int m = tid & 127, cg = tid >> 7;
-                const int y = (m >> 4) + tap / 3, x = (m & 15) + tap % 3;
-                sA[buf][tc_off(m, 8 * cg) >> 4] = halo[(cg * kTcvHH + y) * kTcvHW + x];
+                const int y = (m >> 4) + dy, x = m & 15;
+                const uint4* hrow = halo + (cg * kTcvHH + y) * kTcvHW + x;
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) sA[buf][dx][tc_off(m, 8 * cg) >> 4] = hrow[dx];
             }
-            const uint4* wsrc = wpk + (long)(tap * nchunk + ch) * COUT * 2;
-            for (int q = tid; q < COUT * 2; q += 256) sB[buf][q] = wsrc[q];
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                const uint4* wsrc = wpk + (long)((3 * dy + dx) * nchunk + ch) * cout_total * 2 + oc0 * 2;
+                for (int q = tid; q < COUT * 2; q += 256) sB[buf][dx][q] = wsrc[q];
+            }
             fence_async_smem();
             tc_fence_before();
             __syncthreads();
             if (s_abort) { ok = false; break; }
             if (tid == 0) {
                 tc_fence_after();
-                umma_f16(taddr, smem_desc(smem_u32(&sA[buf][0]), 128, 256), smem_desc(smem_u32(&sB[buf][0]), 128, 256),
-                         idesc, s > 0 ? 1u : 0u);
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx)
+                    umma_f16(taddr, smem_desc(smem_u32(&sA[buf][dx][0]), 128, 256),
+                             smem_desc(smem_u32(&sB[buf][dx][0]), 128, 256), idesc, (s > 0 || dx > 0) ? 1u : 0u);
                 umma_commit(&bar[buf]);
             }
         }
@@ -249,9 +260,9 @@ __global__ void __launch_bounds__(256) k_conv3_tc(const void* __restrict__ in_, 
             if (pin) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const long off = (long)b * out_bs + (long)(o0 + j) * plane + (long)y * W + x;
+                    const long off = (long)b * out_bs + (long)(oc0 + o0 + j) * plane + (long)y * W + x;
                     if (MODE == 0)
-                        ((bf16*)out_)[off] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[j]) + bias[o0 + j], 0.f));
+                        ((bf16*)out_)[off] = __float2bfloat16_rn(fmaxf(__uint_as_float(v[j]) + bias[oc0 + o0 + j], 0.f));
                     else
                         ((float*)out_)[off] = __uint_as_float(v[j]);
                 }
@@ -732,6 +743,7 @@ struct tnlm_unet {
     tnlm::unet::bf16* wtct = nullptr;                               // same for the input gradients
     std::vector<long> tcofft;
     int* derr = nullptr;                                            // device error flags
+    int num_sms = 148;
     long adam_t = 0;
     // activations (BF16) and gradient scratch (FP32), sized for cap_pixels * batch
     long cap = 0;
@@ -844,6 +856,26 @@ void conv3(const TIN* in, long in_bs, int Cin, const bf16* mask, long mask_bs, c
                                                  Cout, H, W);
 }
 
+// Output channels per CTA of the tensor-core convolution: 64 (32 when the
+// count is not a multiple of 64, or when 64 would not fill twice the SMs);
+// with three taps per step double-buffered this keeps the static shared
+// memory under 48 KB.
+int tc_n_tile(int cout, int ctas, int sms) {
+    int nt = cout % 64 == 0 ? 64 : 32;
+    if (nt == 64 && (long)ctas * (cout / 64) < 2L * sms) nt = 32;
+    return nt;
+}
+
+template <int MODE>
+bool tc_launch(int nt, dim3 grid, cudaStream_t st, const void* in, long in_bs, int cin, const bf16* mask, long m_bs,
+               const uint4* wp, const float* bias, void* out, long out_bs, int H, int W, int tx, int cout, int* err) {
+    switch (nt) {
+        case 32: k_conv3_tc<32, MODE><<<grid, 256, 0, st>>>(in, in_bs, cin, mask, m_bs, wp, bias, out, out_bs, H, W, tx, cout, err); return true;
+        case 64: k_conv3_tc<64, MODE><<<grid, 256, 0, st>>>(in, in_bs, cin, mask, m_bs, wp, bias, out, out_bs, H, W, tx, cout, err); return true;
+        default: return false;
+    }
+}
+
 // Forward 3x3 layer: the tensor-core kernel for 32/64/128/256 output
 // channels, the CUDA-core one otherwise.
 void conv3_fwd(tnlm_unet* n, int li, const bf16* in, long in_bs, int Cin, bf16* out, long out_bs, int Cout,
@@ -852,15 +884,12 @@ void conv3_fwd(tnlm_unet* n, int li, const bf16* in, long in_bs, int Cin, bf16* 
     const long to = n->tcoff[li];
     if (to >= 0) {
         const int tx = (W + kTcvTW - 1) / kTcvTW, ty = (H + kTcvTH - 1) / kTcvTH;
-        dim3 grid(tx * ty, B);
+        const int nt = tc_n_tile(Cout, tx * ty * B, n->num_sms);
+        dim3 grid(tx * ty, B, Cout / nt);
         const uint4* wp = (const uint4*)(n->wtc + to);
-        switch (Cout) {
-            case 32: k_conv3_tc<32, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
-            case 64: k_conv3_tc<64, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
-            case 128: k_conv3_tc<128, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
-            case 256: k_conv3_tc<256, 0><<<grid, 256, 0, st>>>(in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, n->derr); return;
-            default: break;
-        }
+        if (tc_launch<0>(nt, grid, st, in, in_bs, Cin, nullptr, 0, wp, n->w + Ly.boff, out, out_bs, H, W, tx, Cout,
+                         n->derr))
+            return;
     }
     conv3<bf16, true, true>(in, in_bs, Cin, nullptr, 0, n->wb + Ly.woff, n->w + Ly.boff, out, out_bs, Cout, H, W, B, st);
 }
@@ -874,15 +903,12 @@ void conv3_dgrad(tnlm_unet* n, int li, const float* g, long g_bs, const bf16* ma
     const long to = n->tcofft[li];
     if (to >= 0) {
         const int tx = (W + kTcvTW - 1) / kTcvTW, ty = (H + kTcvTH - 1) / kTcvTH;
-        dim3 grid(tx * ty, B);
+        const int nt = tc_n_tile(Ly.cin, tx * ty * B, n->num_sms);
+        dim3 grid(tx * ty, B, Ly.cin / nt);
         const uint4* wp = (const uint4*)(n->wtct + to);
-#define TNLM_DG(C) \
-    case C: k_conv3_tc<C, 1><<<grid, 256, 0, st>>>(g, g_bs, Ly.cout, mask, m_bs, wp, nullptr, out, out_bs, H, W, tx, n->derr); return;
-        switch (Ly.cin) {
-            TNLM_DG(32) TNLM_DG(64) TNLM_DG(96) TNLM_DG(128) TNLM_DG(192) TNLM_DG(256)
-            default: break;
-        }
-#undef TNLM_DG
+        if (tc_launch<1>(nt, grid, st, g, g_bs, Ly.cout, mask, m_bs, wp, nullptr, out, out_bs, H, W, tx, Ly.cin,
+                         n->derr))
+            return;
     }
     conv3<float, false, false>(g, g_bs, Ly.cout, mask, m_bs, n->wt + Ly.woff, nullptr, out, out_bs, Ly.cin, H, W, B, st);
 }
@@ -936,8 +962,16 @@ tnlm_status conv3_param_grads(tnlm_unet* n, const Layer& Ly, const float* gout, 
                               const bf16* act, long a_bs, const TIN* in, long in_bs, int H, int W, int B,
                               cudaStream_t st) {
     const long rows = (long)B * H;
-    const int S = (int)(rows < 64 ? rows : 64);
+    const bool tc = sizeof(TIN) == 2 && W % 16 == 0;
+    // row slices: the tensor-core kernel gets enough CTAs for ~4 per SM
+    long S = rows < 64 ? rows : 64;
+    if (tc) {
+        const long per = (long)((Ly.cin + 15) / 16) * ((Ly.cout + 127) / 128);
+        S = (4L * n->num_sms + per - 1) / per;
+        S = S < 1 ? 1 : (S > rows ? rows : S);
+    }
     const int rows_per = (int)((rows + S - 1) / S);
+    S = (rows + rows_per - 1) / rows_per;
     const long nw = (long)Ly.cout * Ly.cin * 9;
     if ((long)S * nw > n->part_cap) {
         cudaFree(n->parts);
@@ -945,16 +979,16 @@ tnlm_status conv3_param_grads(tnlm_unet* n, const Layer& Ly, const float* gout, 
         UCK(cudaMalloc(&n->parts, sizeof(float) * S * nw), "gradient partials");
         n->part_cap = (long)S * nw;
     }
-    if (sizeof(TIN) == 2 && W % 16 == 0) {
-        dim3 grid((Ly.cin + 15) / 16, (Ly.cout + 127) / 128, S);
+    if (tc) {
+        dim3 grid((Ly.cin + 15) / 16, (Ly.cout + 127) / 128, (unsigned)S);
         k_conv3_wgrad_tc<<<grid, 256, 0, st>>>(gout, g_bs, act, a_bs, (const bf16*)in, in_bs, Ly.cin, Ly.cout, H,
                                                W, B, rows_per, n->parts, n->derr);
     } else {
         const int blocks = ((Ly.cout + 15) / 16) * ((Ly.cin + 15) / 16);
-        k_conv3_wgrad<TIN><<<dim3(blocks, S), 256, 0, st>>>(gout, g_bs, act, a_bs, in, in_bs, Ly.cin, Ly.cout,
+        k_conv3_wgrad<TIN><<<dim3(blocks, (unsigned)S), 256, 0, st>>>(gout, g_bs, act, a_bs, in, in_bs, Ly.cin, Ly.cout,
                                                             H, W, B, rows_per, n->parts);
     }
-    k_reduce_parts<<<grid1(nw), 256, 0, st>>>(n->parts, S, nw, n->g + Ly.woff);
+    k_reduce_parts<<<grid1(nw), 256, 0, st>>>(n->parts, (int)S, nw, n->g + Ly.woff);
     k_bias_grad<<<Ly.cout, 256, 0, st>>>(gout, g_bs, act, a_bs, B, (long)H * W, n->g + Ly.boff);
     UCK(cudaGetLastError(), "gradient launch");
     return TNLM_OK;
@@ -1096,6 +1130,7 @@ tnlm_status tnlm_unet_create(int in_ch, int out_ch, int base, int levels, int de
     if (cudaSetDevice(device) != cudaSuccess) return ufail(TNLM_ERR_INVALID_ARG, "device not available");
     tnlm_unet* n = new tnlm_unet();
     n->device = device; n->in_ch = in_ch; n->out_ch = out_ch; n->base = base; n->levels = levels;
+    cudaDeviceGetAttribute(&n->num_sms, cudaDevAttrMultiProcessorCount, device);
     long off = 0;
     auto add = [&](int co, int ci, int k) {
         Layer Ly{co, ci, k, off, off + (long)co * ci * k * k};
