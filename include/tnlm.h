@@ -227,18 +227,23 @@ tnlm_status tnlm_autotune(tnlm_geometry* geom, const tnlm_params* params, const 
 
 /* Batched reconstruction of many independent slices (each its own handle,
  * sizes, view counts and parameters may differ; all on one device).  Each
- * slice runs exactly params[i].k_outer outer iterations of the algorithm box
- * (tol must be 0) from d_f[i], as tnlm_reconstruct would, with bitwise the
- * same result.  One outer iteration of all slices is captured as one CUDA
- * graph with a branch per slice, so kernels of different slices overlap.
- * When every slice has the same k_outer the whole run is ONE graph launch:
- * a conditional WHILE node around that iteration, counted down on the
- * device; otherwise (or if the runtime refuses the loop graph) the
- * iteration graph is replayed once per outer iteration and slices that
- * reach their k_outer leave it.  autotune_shapes != 0 runs tnlm_autotune first
- * on every handle not yet tuned.  reports (may be NULL) is an array of
- * count reports.  Synchronises the stream.  Errors: as tnlm_reconstruct; the
- * first failing slice's status is returned after all reports are filled. */
+ * slice runs the algorithm box from d_f[i] exactly as tnlm_reconstruct
+ * would, with bitwise the same result and the same stopping rule: at most
+ * params[i].k_outer outer iterations, and with tol > 0 it stops at the first
+ * check (every tol_check_every iterations) where the relative change is
+ * below tol.  The whole run is ONE graph launch: a conditional WHILE node
+ * whose body starts with a gate kernel that evaluates every slice's
+ * stopping rule on the device and then runs one conditional IF node per
+ * slice (that slice's outer iteration, captured once), so kernels of
+ * different slices overlap and finished slices drop out without host
+ * round trips.  If the runtime refuses that graph (or the environment
+ * variable TNLM_BATCH_REPLAY is 1), a graph of one outer iteration of the
+ * live slices is replayed instead and the stopping rules are checked on
+ * the host (same results).  autotune_shapes != 0 runs
+ * tnlm_autotune first on every handle not yet tuned.  reports (may be NULL)
+ * is an array of count reports (iterations = that slice's own count).
+ * Synchronises the stream.  Errors: as tnlm_reconstruct; the first failing
+ * slice's status is returned after all reports are filled. */
 tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_params* params,
                                    int count, const float* const* d_y, const float* const* d_winv,
                                    float* const* d_f, tnlm_report* reports, int autotune_shapes,
@@ -277,6 +282,16 @@ const char* tnlm_last_error(void);
 /* Test hook for failure handling: the n-th device allocation from now on
  * (n >= 1) fails as if the device were out of memory; n = 0 disables. */
 void tnlm_debug_fail_alloc_after(int n);
+
+/* Test hook for the timeout path: the pipeline waits of the TMA
+ * Gauss-Jacobi sweep give up after 'polls' polls of their mbarrier (< 0:
+ * the built-in limit, 2^24).  A sweep whose wait gives up stops issuing
+ * copies, waits (with the built-in limit) for the copies it has in flight,
+ * leaves its outputs unwritten and sets the device flag that the next
+ * synchronising call reports as TNLM_ERR_TIMEOUT; the handle stays usable.
+ * Affects launches issued after the call (captured graphs keep the value
+ * they were captured with). */
+void tnlm_debug_wait_limit(long polls);
 
 #ifdef __cplusplus
 }

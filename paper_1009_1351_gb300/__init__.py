@@ -28,7 +28,7 @@ TNLM_DATA_GRAD = 1
 
 EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tnlm_backproject",
             "tnlm_weights_size", "tnlm_weights", "tnlm_workspace_bytes", "tnlm_reconstruct",
-            "tnlm_last_error", "tnlm_debug_fail_alloc_after", "tnlm_profile_enable",
+            "tnlm_last_error", "tnlm_debug_fail_alloc_after", "tnlm_debug_wait_limit", "tnlm_profile_enable",
             "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp", "tnlm_autotune",
             "tnlm_reconstruct_batch", "tnlm_batch_last_was_loop", "tnlm_fbp_phases", "tnlm_unet_create", "tnlm_unet_destroy", "tnlm_unet_param_count",
             "tnlm_unet_set_params", "tnlm_unet_get_params", "tnlm_unet_forward", "tnlm_unet_grads",
@@ -114,6 +114,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_last_error.restype = ctypes.c_char_p
     lib.tnlm_debug_fail_alloc_after.argtypes = [ctypes.c_int]
     lib.tnlm_debug_fail_alloc_after.restype = None
+    lib.tnlm_debug_wait_limit.argtypes = [ctypes.c_long]
+    lib.tnlm_debug_wait_limit.restype = None
     lib.tnlm_profile_enable.argtypes = [vp, ctypes.c_uint]
     lib.tnlm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double),
                                       ctypes.POINTER(ctypes.c_longlong), ctypes.c_int]
@@ -287,9 +289,11 @@ def tnlm_autotune(geom: Geometry, params, y, winv, f0, stream=None) -> Dict[str,
 
 def tnlm_reconstruct_batch(geoms, params, ys, winvs, fs, autotune: bool = True,
                            stream=None) -> List[Dict[str, Any]]:
-    """Run the TNLM iteration in place on every f of the batch (one CUDA
-    graph per outer iteration for all slices).  params: one parameter set or
-    one per slice (fixed k_outer, tol = 0).  Returns one report per slice."""
+    """Run the TNLM iteration in place on every f of the batch as one graph
+    launch (each slice stops at its own k_outer or tolerance, decided on the
+    device).  params: one parameter set or one per slice (objects with the
+    tnlm_params fields; tol and tol_check_every optional).  Returns one
+    report per slice."""
     n = len(geoms)
     if not (len(ys) == len(winvs) == len(fs) == n):
         raise ValueError("geoms, ys, winvs and fs must have the same length")
@@ -327,6 +331,12 @@ def tnlm_batch_last_was_loop() -> bool:
 
 def tnlm_debug_fail_alloc_after(n: int) -> None:
     load_library().tnlm_debug_fail_alloc_after(int(n))
+
+
+def tnlm_debug_wait_limit(polls: int) -> None:
+    """Poll limit of the TMA sweep's pipeline waits (< 0: built-in); a test
+    hook for the timeout path."""
+    load_library().tnlm_debug_wait_limit(int(polls))
 
 
 def tnlm_profile_enable(geom: Geometry, classes=()) -> None:

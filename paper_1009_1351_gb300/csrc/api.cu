@@ -2,6 +2,8 @@
 // the outer iteration of the TNLM algorithm box (Sec. 2.2).
 #include "internal.cuh"
 
+#include <stdlib.h>
+
 #include <math.h>
 #include <stdarg.h>
 #include <stdint.h>
@@ -147,7 +149,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Byte layout of the workspace for window radius rho and history capacity kcap.
 struct WsLayout {
     size_t off_u, off_s, off_gr, off_R, off_T, off_r, off_z, off_t, off_sw, off_bps, off_D, off_U0, off_U1,
-        off_mins, off_zn, off_part, off_part2, off_state, total;
+        off_mins, off_zn, off_part, off_part2, off_gjs, off_gjc, off_state, total;
     size_t part_len, part2_len;
     PadPlane pp;
 };
@@ -187,6 +189,8 @@ WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
     L.part2_len = 2 * (size_t)gj_blocks(g);
     L.off_part = take(8 * L.part_len);
     L.off_part2 = take(8 * L.part2_len);
+    L.off_gjs = take(4 * gj_split_floats(g));
+    L.off_gjc = take(4 * (size_t)gj_blocks(g));
     // state: gamma, a, b, res0 [N] doubles; hist 2 x kcap doubles; active [N], iter, err ints
     L.off_state = take(8 * (4 * N + 2 * (size_t)kcap) + 4 * (N + 2));
     L.total = o;
@@ -235,6 +239,8 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     ws.part = (double*)(b + L.off_part);
     ws.part_len = L.part_len;
     ws.part2 = (double*)(b + L.off_part2);
+    ws.gjsum = (float*)(b + L.off_gjs);
+    ws.gjcnt = (int*)(b + L.off_gjc);
     const size_t N = g->N;
     double* sd = (double*)(b + L.off_state);
     ws.st.gamma = sd;
@@ -506,13 +512,34 @@ tnlm_status autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y, c
 // iteration, so kernels of different slices run side by side.  When slices
 // with fewer iterations finish, the graph is re-captured without them.
 // ---------------------------------------------------------------------------
-// Device-side loop of the batched graph: the body ends with a tick that
-// counts the outer iterations down and keeps the WHILE node running until
-// the count reaches zero.
-__global__ void k_loop_set(int* counter, int k) { *counter = k; }
-__global__ void k_loop_tick(cudaGraphConditionalHandle h, int* counter) {
-    const int c = --(*counter);
-    cudaGraphSetConditional(h, c > 0 ? 1u : 0u);
+// Device-side control of the batched loop graph.  Per slice: its own
+// iteration counter and its stopping rule (k_outer; tol checked every
+// 'every' iterations, the rule tnlm_reconstruct applies on the host).
+struct GateSlice {
+    const int* iter;
+    const double* hist_rel;
+    double tol;
+    int k_outer;
+    int every;
+};
+
+// Runs at the top of every pass of the WHILE body: sets each slice's IF
+// condition (does it take another outer iteration?) and the WHILE
+// condition (does any slice?).  A pass where no slice runs is the last.
+__global__ void k_batch_gate(const GateSlice* __restrict__ s, const cudaGraphConditionalHandle* __restrict__ hs,
+                             int n, cudaGraphConditionalHandle hw) {
+    int any = 0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const GateSlice q = s[j];
+        const int done = *q.iter;
+        bool run = done < q.k_outer;
+        if (run && q.tol > 0.0 && done > 0 && done % q.every == 0 && q.hist_rel[done - 1] < q.tol)
+            run = false;
+        cudaGraphSetConditional(hs[j], run ? 1u : 0u);
+        any |= run ? 1 : 0;
+    }
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) cudaGraphSetConditional(hw, any ? 1u : 0u);
 }
 
 struct BatchItem {
@@ -535,11 +562,15 @@ struct BatchState {
     cudaGraphExec_t exec = nullptr;
     std::vector<BatchItem> key;
     std::vector<std::array<long long, TNLM_KCLASS_COUNT>> launches;   // per slice and replay
-    // the whole K-iteration run as one launch: a WHILE node around the body
+    // the whole run as one launch: a WHILE node around a gate kernel and one
+    // IF node per slice (that slice's outer iteration)
     cudaGraphExec_t loop_exec = nullptr;
     std::vector<BatchItem> loop_key;
     bool loop_broken = false;          // the runtime refused the loop graph once: use replays
-    int* counter = nullptr;
+    GateSlice* gate = nullptr;                       // device [gate_cap]
+    cudaGraphConditionalHandle* gate_h = nullptr;    // device [gate_cap]
+    size_t gate_cap = 0;
+    std::vector<cudaGraphConditionalHandle> handles;  // the loop graph's IF handles
     std::vector<std::array<long long, TNLM_KCLASS_COUNT>> loop_launches;   // per slice and iteration
 };
 std::mutex g_batch_mu;
@@ -587,27 +618,41 @@ tnlm_status batch_resources(BatchState* B, size_t n) {
         CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "batch event");
         B->events.push_back(ev);
     }
-    if (!B->counter) {
+    if (B->gate_cap < n) {
+        if (B->gate) cudaFree(B->gate);
+        if (B->gate_h) cudaFree(B->gate_h);
+        B->gate = nullptr;
+        B->gate_h = nullptr;
+        B->gate_cap = 0;
         void* p = nullptr;
-        CK(dev_alloc(&p, sizeof(int)), "loop counter");
-        B->counter = (int*)p;
+        CK(dev_alloc(&p, sizeof(GateSlice) * n), "batch gate");
+        B->gate = (GateSlice*)p;
+        CK(dev_alloc(&p, sizeof(cudaGraphConditionalHandle) * n), "batch gate");
+        B->gate_h = (cudaGraphConditionalHandle*)p;
+        B->gate_cap = n;
     }
     B->launches.assign(n, {});
     return TNLM_OK;
 }
 
-// All K outer iterations of all slices as ONE graph launch: a conditional
-// WHILE node whose body is one outer iteration of every slice plus a tick
-// kernel that counts down.  Returns TNLM_OK with *built = false when the
-// runtime does not accept the loop graph (the caller then replays the
-// single-iteration graph K times).
+// The whole batched run as ONE graph launch: a conditional WHILE node whose
+// body is a gate kernel followed by one conditional IF node per slice, the
+// IF body being that slice's outer iteration.  The gate decides on the
+// device which slices take another iteration (k_outer, tolerance), so
+// slices with different iteration counts or tolerances all run in the one
+// launch.  Returns TNLM_OK with *built = false when the runtime does not
+// accept the loop graph (the caller then replays the single-iteration
+// graph).
 tnlm_status loop_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
                        const std::vector<const tnlm_params*>& ps, const std::vector<const float*>& ys,
                        const std::vector<float*>& fs, bool* built) {
     *built = false;
     if (B->loop_broken) return TNLM_OK;
-    std::vector<BatchItem> key(gs.size());
-    for (size_t j = 0; j < gs.size(); ++j)
+    const char* env = getenv("TNLM_BATCH_REPLAY");     // force the replay path
+    if (env && env[0] == '1') return TNLM_OK;
+    const size_t n = gs.size();
+    std::vector<BatchItem> key(n);
+    for (size_t j = 0; j < n; ++j)
         key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws.base, ys[j], fs[j], *ps[j]};
     if (B->loop_exec && key == B->loop_key) {
         *built = true;
@@ -617,52 +662,79 @@ tnlm_status loop_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
         cudaGraphExecDestroy(B->loop_exec);
         B->loop_exec = nullptr;
     }
-    tnlm_status s = batch_resources(B, gs.size());
+    tnlm_status s = batch_resources(B, n);
     if (s != TNLM_OK) return s;
     cudaGraph_t graph = nullptr;
-    cudaGraphConditionalHandle h;
+    cudaGraphConditionalHandle hw;
     cudaGraphNodeParams np = {};
-    cudaGraphNode_t node;
+    cudaGraphNode_t node, gate;
+    std::vector<cudaGraphConditionalHandle> hs(n);
+    cudaGraph_t body = nullptr;
     cudaError_t e = cudaGraphCreate(&graph, 0);
-    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault);
     if (e == cudaSuccess) {
         np.type = cudaGraphNodeTypeConditional;
-        np.conditional.handle = h;
+        np.conditional.handle = hw;
         np.conditional.type = cudaGraphCondTypeWhile;
         np.conditional.size = 1;
         e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        if (e == cudaSuccess) body = np.conditional.phGraph_out[0];
     }
-    if (e == cudaSuccess)
-        e = cudaStreamBeginCaptureToGraph(B->cap, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        if (graph) cudaGraphDestroy(graph);
-        B->loop_broken = true;
-        return TNLM_OK;
+    for (size_t j = 0; j < n && e == cudaSuccess; ++j)
+        e = cudaGraphConditionalHandleCreate(&hs[j], body, 0, 0);
+    if (e == cudaSuccess) {
+        const GateSlice* a0 = B->gate;
+        const cudaGraphConditionalHandle* a1 = B->gate_h;
+        int a2 = (int)n;
+        cudaGraphConditionalHandle a3 = hw;
+        void* args[] = {&a0, &a1, &a2, &a3};
+        cudaKernelNodeParams kp = {};
+        kp.func = (void*)k_batch_gate;
+        kp.gridDim = dim3(1);
+        kp.blockDim = dim3(256);
+        kp.kernelParams = args;
+        e = cudaGraphAddKernelNode(&gate, body, nullptr, 0, &kp);
     }
-    cudaError_t ce = cudaSuccess;
-    s = capture_body(B, gs, ps, ys, fs, &ce);
-    if (s == TNLM_OK && ce == cudaSuccess) {
-        k_loop_tick<<<1, 1, 0, B->cap>>>(h, B->counter);
-        ce = cudaGetLastError();
+    for (size_t j = 0; j < n && e == cudaSuccess && s == TNLM_OK; ++j) {
+        cudaGraphNodeParams ip = {};
+        ip.type = cudaGraphNodeTypeConditional;
+        ip.conditional.handle = hs[j];
+        ip.conditional.type = cudaGraphCondTypeIf;
+        ip.conditional.size = 1;
+        cudaGraphNode_t ifn;
+        e = cudaGraphAddNode(&ifn, body, &gate, nullptr, 1, &ip);
+        if (e == cudaSuccess)
+            e = cudaStreamBeginCaptureToGraph(B->cap, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) break;
+        tnlm_geometry* g = gs[j];
+        long long before[TNLM_KCLASS_COUNT];
+        for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) before[c] = g->launches[c];
+        const unsigned mask = g->prof_mask;
+        g->prof_mask = 0;
+        s = outer_iteration(g, ps[j], ys[j], fs[j], B->cap);
+        g->prof_mask = mask;
+        for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) {
+            B->launches[j][c] = g->launches[c] - before[c];
+            g->launches[c] = before[c];
+        }
+        cudaGraph_t out = nullptr;
+        e = cudaStreamEndCapture(B->cap, &out);
     }
-    cudaGraph_t body_out = nullptr;
-    const cudaError_t ee = cudaStreamEndCapture(B->cap, &body_out);
     if (s != TNLM_OK) {
-        cudaGraphDestroy(graph);
+        if (graph) cudaGraphDestroy(graph);
         return s;
     }
-    if (ce == cudaSuccess && ee == cudaSuccess) ce = cudaGraphInstantiate(&B->loop_exec, graph, 0);
-    else if (ce == cudaSuccess) ce = ee;
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) {
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&B->loop_exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
         cudaGetLastError();
         B->loop_exec = nullptr;
         B->loop_broken = true;
         return TNLM_OK;
     }
     B->loop_key = key;
+    B->handles = hs;
     B->loop_launches = B->launches;
     *built = true;
     return TNLM_OK;
@@ -726,8 +798,11 @@ tnlm_status read_report(tnlm_geometry* g, int done, tnlm_report* rep, cudaStream
     }
     if (err) {
         CK(cudaMemsetAsync(ws.st.err, 0, sizeof(int), st), "reset");
-        if (err & 16)   // a bounded wait of the TMA sweep ran out
+        if (err & 16) {   // a bounded wait of the TMA sweep ran out
+            // a sweep that stopped early may leave half-done tile counters
+            CK(cudaMemsetAsync(ws.gjcnt, 0, sizeof(int) * (size_t)gj_blocks(g), st), "reset");
             return fail(TNLM_ERR_TIMEOUT, "a device-side wait timed out (flags 0x%x)", err);
+        }
         return fail(TNLM_ERR_NUMERIC, "non-finite value met on the device (flags 0x%x)", err);
     }
     return TNLM_OK;
@@ -741,6 +816,8 @@ extern "C" {
 const char* tnlm_last_error(void) { return g_err; }
 
 void tnlm_debug_fail_alloc_after(int n) { g_fail_after.store(n > 0 ? n : 0); }
+
+void tnlm_debug_wait_limit(long polls) { g_gj_wait_limit = polls >= 0 ? polls : kSpinLimit; }
 
 tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** out) {
     g_err[0] = 0;
@@ -1141,8 +1218,6 @@ tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_param
         if (!geoms[i]) return fail(TNLM_ERR_INVALID_ARG, "geometry %d is NULL", i);
         tnlm_status s = check_params(&params[i]);
         if (s != TNLM_OK) return s;
-        if (params[i].tol != 0.0)
-            return fail(TNLM_ERR_INVALID_ARG, "batched slices run a fixed number of iterations (tol must be 0)");
         if (!d_y[i] || !d_winv[i] || !d_f[i]) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer of slice %d", i);
         if (!aligned16(d_y[i]) || !aligned16(d_winv[i]) || !aligned16(d_f[i]))
             return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned (slice %d)", i);
@@ -1155,6 +1230,7 @@ tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_param
     DeviceGuard dg(dev);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
     cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> done(count, 0);
     for (int i = 0; i < count; ++i) {
         tnlm_geometry* g = geoms[i];
         const tnlm_params* p = &params[i];
@@ -1177,41 +1253,69 @@ tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_param
         std::vector<const float*> ys;
         std::vector<float*> fs;
         g_last_batch_loop = 0;
-        bool same_k = kmax > 0;
-        for (int i = 0; i < count; ++i) same_k = same_k && params[i].k_outer == kmax;
-        if (same_k) {
-            for (int i = 0; i < count; ++i) {
-                gs.push_back(geoms[i]); ps.push_back(&params[i]); ys.push_back(d_y[i]); fs.push_back(d_f[i]);
-            }
-            bool built = false;
-            tnlm_status s = loop_graph(B, gs, ps, ys, fs, &built);
-            if (s != TNLM_OK) return s;
-            if (built) {
-                k_loop_set<<<1, 1, 0, st>>>(B->counter, kmax);
-                CK(cudaGetLastError(), "loop counter");
-                CK(cudaGraphLaunch(B->loop_exec, st), "batch loop graph launch");
-                for (size_t j = 0; j < gs.size(); ++j)
-                    for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) gs[j]->launches[c] += kmax * B->loop_launches[j][c];
-                kmax = 0;     // done: skip the per-iteration replays below
-                g_last_batch_loop = 1;
-            }
+        for (int i = 0; i < count; ++i) {
+            gs.push_back(geoms[i]); ps.push_back(&params[i]); ys.push_back(d_y[i]); fs.push_back(d_f[i]);
         }
+        bool built = false;
+        tnlm_status s = kmax > 0 ? loop_graph(B, gs, ps, ys, fs, &built) : TNLM_OK;
+        if (s != TNLM_OK) return s;
+        if (built) {
+            std::vector<GateSlice> gh(count);
+            for (int i = 0; i < count; ++i)
+                gh[i] = {geoms[i]->ws.st.iter, geoms[i]->ws.st.hist_rel, params[i].tol, params[i].k_outer,
+                         params[i].tol > 0.0 ? params[i].tol_check_every : 1};
+            CK(cudaMemcpyAsync(B->gate, gh.data(), sizeof(GateSlice) * count, cudaMemcpyHostToDevice, st),
+               "batch gate upload");
+            CK(cudaMemcpyAsync(B->gate_h, B->handles.data(), sizeof(cudaGraphConditionalHandle) * count,
+                               cudaMemcpyHostToDevice, st), "batch gate upload");
+            CK(cudaGraphLaunch(B->loop_exec, st), "batch loop graph launch");
+            for (int i = 0; i < count; ++i)
+                CK(cudaMemcpyAsync(&done[i], geoms[i]->ws.st.iter, sizeof(int), cudaMemcpyDeviceToHost, st),
+                   "readback");
+            CK(cudaStreamSynchronize(st), "sync");
+            for (int i = 0; i < count; ++i)
+                for (int c = 0; c < TNLM_KCLASS_COUNT; ++c)
+                    geoms[i]->launches[c] += (long long)done[i] * B->loop_launches[i][c];
+            kmax = 0;     // done: skip the per-iteration replays below
+            g_last_batch_loop = 1;
+        }
+        // replays of the single-iteration graph; slices leave it at their
+        // k_outer or once their stopping rule holds (checked on the host)
+        std::vector<char> live(count, 1);
         for (int k = 0; k < kmax; ++k) {
             gs.clear(); ps.clear(); ys.clear(); fs.clear();
+            std::vector<int> idx;
             for (int i = 0; i < count; ++i)
-                if (k < params[i].k_outer) {
+                if (live[i] && k < params[i].k_outer) {
+                    idx.push_back(i);
                     gs.push_back(geoms[i]); ps.push_back(&params[i]); ys.push_back(d_y[i]); fs.push_back(d_f[i]);
                 }
-            tnlm_status s = batch_graph(B, gs, ps, ys, fs);
+            if (idx.empty()) break;
+            s = batch_graph(B, gs, ps, ys, fs);
             if (s != TNLM_OK) return s;
             CK(cudaGraphLaunch(B->exec, st), "batch graph launch");
             for (size_t j = 0; j < gs.size(); ++j)
                 for (int c = 0; c < TNLM_KCLASS_COUNT; ++c) gs[j]->launches[c] += B->launches[j][c];
+            std::vector<int> chk;
+            for (int i : idx) {
+                done[i] = k + 1;
+                if (params[i].tol > 0.0 && done[i] % params[i].tol_check_every == 0 && done[i] < params[i].k_outer)
+                    chk.push_back(i);
+            }
+            if (!chk.empty()) {
+                std::vector<double> rel(chk.size());
+                for (size_t j = 0; j < chk.size(); ++j)
+                    CK(cudaMemcpyAsync(&rel[j], geoms[chk[j]]->ws.st.hist_rel + k, sizeof(double),
+                                       cudaMemcpyDeviceToHost, st), "readback");
+                CK(cudaStreamSynchronize(st), "sync");
+                for (size_t j = 0; j < chk.size(); ++j)
+                    if (rel[j] < params[chk[j]].tol) live[chk[j]] = 0;
+            }
         }
     }
     tnlm_status first = TNLM_OK;
     for (int i = 0; i < count; ++i) {
-        tnlm_status s = read_report(geoms[i], params[i].k_outer, reports ? &reports[i] : nullptr, st);
+        tnlm_status s = read_report(geoms[i], done[i], reports ? &reports[i] : nullptr, st);
         if (s != TNLM_OK && first == TNLM_OK) first = s;
     }
     return first;

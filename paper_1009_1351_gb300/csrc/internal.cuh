@@ -71,6 +71,8 @@ struct Workspace {
     double* part = nullptr;  // partial sums
     size_t part_len = 0;
     double* part2 = nullptr; // second partial array (relative change)
+    float* gjsum = nullptr;  // TMA sweep: partial sums of window halves [tile][2][4][256] float4
+    int* gjcnt = nullptr;    // TMA sweep: halves done per tile (0 between sweeps)
     DevState st{};
     // TMA descriptors of the distance planes [N*W2max][py][px]: boxes of
     // 64 x 16 (forward rows) and 68 x 16 (backward rows) floats
@@ -100,6 +102,7 @@ struct tnlm_geometry {
     // changes whenever they do, so captured graphs are re-captured
     int tune_bp_groups = 0;     // view groups (CTAs) per backprojection tile
     int tune_gj_tpb = 0;        // tiles per CTA of the TMA sweep
+    int tune_gj_split = 0;      // window halves per tile of the TMA sweep (0: by wave fill)
     unsigned tune_gen = 0;
     unsigned long long uid = 0; // unique per handle (graph and batch keys)
     // CUDA graph of one outer iteration (see api.cu)
@@ -173,6 +176,11 @@ cudaError_t launch_finalize_nogj(const tnlm_geometry* g, const Workspace& ws, co
 cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks,
                                 cudaStream_t st);
 int gj_blocks(const tnlm_geometry* g);
+int gj_tma_split(const tnlm_geometry* g);
+// Poll limit of the TMA sweep's pipeline waits (not of its final drain);
+// lowered only by tnlm_debug_wait_limit to exercise the timeout path.
+extern long g_gj_wait_limit;
+size_t gj_split_floats(const tnlm_geometry* g);
 cudaError_t launch_weights_norm(const tnlm_geometry* g, const Workspace& ws, int window,
                                 double h, cudaStream_t st);
 cudaError_t launch_weights_export(const tnlm_geometry* g, const Workspace& ws, int window,
@@ -240,8 +248,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
         : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
-    for (long it = 0; it < kSpinLimit; ++it)
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, long limit = kSpinLimit) {
+    for (long it = 0; it < limit; ++it)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

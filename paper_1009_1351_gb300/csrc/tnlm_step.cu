@@ -515,6 +515,17 @@ __global__ void __launch_bounds__(kGjvTx * kGjvTy) k_gj_vec(GjArgs a) {
 // "full" mbarrier (expected bytes) and an "empty" one (one arrival per
 // consumer warp); every wait is bounded and a timeout ends the block with an
 // error flag after draining its copies.
+//
+// Work units.  With split = 2 a (tile, phase) is two units, each taking half
+// of the window rows (rows [0, (W+1)/2) and the rest), so that the number of
+// units fills the resident CTA slots in whole waves where (tile, phase)
+// alone would leave a partial last wave.  Each half stores its four partial
+// sums per pixel in a scratch slot; the half that arrives second (a counter
+// per tile, no waiting) adds the other's sums to its own -- one FP32
+// addition, which is commutative, so the result does not depend on the
+// arrival order -- and finishes the pixels.  The relative-change partials
+// are written per (tile, phase), so they do not depend on split or on the
+// tiles per CTA either.
 // ---------------------------------------------------------------------------
 constexpr int kTmaTW = 64, kTmaTH = 16;
 constexpr int kTmaBW = kTmaTW + 4;
@@ -544,11 +555,32 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// Barrier 1 of the consumer warps only (the producer warp never joins it).
+// Every consumer thread reaches each of these barriers the same number of
+// times: a wait that timed out does not leave the unit loop on its own, the
+// consumers leave it together after consumer_sync_or agrees to stop.
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kTmaConsumers) : "memory");
+}
+__device__ __forceinline__ bool consumer_sync_or(bool v) {
+    unsigned r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((unsigned)v), "n"(kTmaConsumers)
+        : "memory");
+    return r != 0;
+}
+
 template <int W, int MODE>
 __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __grid_constant__ CUtensorMap tmF,
                                                         const __grid_constant__ CUtensorMap tmB,
                                                         const __grid_constant__ CUtensorMap tmU,
-                                                        int tpb) {
+                                                        int tpb, int split, float4* __restrict__ hsum,
+                                                        int* __restrict__ hcnt, long wlim) {
     constexpr int RHO = (W - 1) / 2;
     constexpr int UOFF = 4 * ((RHO + 3) / 4);
     constexpr int NCH = (2 * UOFF + 4) / 4;     // float4 chunks of a window row
@@ -561,15 +593,16 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
     uint64_t* empty = full + kTmaStages;
     uint64_t* ufull = empty + kTmaStages;                      // [2]
     uint64_t* uempty = ufull + 2;                              // [2]
-    __shared__ int s_abort, s_issued, s_uissued;
+    __shared__ int s_abort, s_issued, s_uissued, s_second;
     __shared__ double wsum[2][kTmaConsumers / 32];
     const int N = a.N, nx = a.nx, ny = a.ny;
     const int tilesx = (nx + kTmaTW - 1) / kTmaTW;
-    const int ntiles = tilesx * ((ny + kTmaTH - 1) / kTmaTH) * N;
-    // tiles blockIdx.x, + gridDim.x, ...: the tiles in flight at any moment
+    const int nunits = tilesx * ((ny + kTmaTH - 1) / kTmaTH) * N * split;
+    // units blockIdx.x, + gridDim.x, ...: the units in flight at any moment
     // stay a contiguous run of the tile-major, phase-minor order, so the
     // second read of each distance plane is served by L2
-    const int t0 = blockIdx.x, tstep = gridDim.x, t1 = min(ntiles, t0 + tpb * tstep);
+    const int t0 = blockIdx.x, tstep = gridDim.x, t1 = min(nunits, t0 + tpb * tstep);
+    constexpr int RMID = (W + 1) / 2;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int px = a.pp.px;
     const size_t plane = a.pp.plane;
@@ -593,14 +626,16 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
         if (lane == 0) {   // producer: runs ahead across the block's tiles
             int kk = 0, nu = 0;
             bool ok = true;
-            for (int t = t0, u = 0; t < t1 && ok; t += tstep, ++u) {
+            for (int q = t0, u = 0; q < t1 && ok; q += tstep, ++u) {
                 const int ub = u % kTmaUBufs;
+                const int t = q / split, half = q - t * split;
+                const int k0 = half ? RMID * W : 0, k1 = (split == 1 || half) ? NK : RMID * W;
                 const int tile = t / N, i = t % N;
                 const int X0 = (tile % tilesx) * kTmaTW, Y0 = (tile / tilesx) * kTmaTH;
                 const int ip = (i + N - 1) % N, inx = (i + 1) % N;
                 // iterate tiles of both neighbour phases (rows/columns outside the plane read 0)
                 if (u >= kTmaUBufs &&
-                    !mbar_wait_bounded(&uempty[ub], (unsigned)(((u - kTmaUBufs) / kTmaUBufs) & 1))) {
+                    !mbar_wait_bounded(&uempty[ub], (unsigned)(((u - kTmaUBufs) / kTmaUBufs) & 1), wlim)) {
                     ok = false;
                     break;
                 }
@@ -609,10 +644,10 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
                 tma_load_3d(ut, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, inx, &ufull[ub]);
                 tma_load_3d(ut + kTmaUFloats, &tmU, X0 + a.pp.ox - 8, Y0 + a.pp.oy - 7, ip, &ufull[ub]);
                 nu = u + 1;
-                for (int k = 0; k < NK; ++k) {
+                for (int k = k0; k < k1; ++k) {
                     const int slot = kk % kTmaStages;
                     if (kk >= kTmaStages &&
-                        !mbar_wait_bounded(&empty[slot], (unsigned)((kk / kTmaStages - 1) & 1))) {
+                        !mbar_wait_bounded(&empty[slot], (unsigned)((kk / kTmaStages - 1) & 1), wlim)) {
                         ok = false;
                         break;
                     }
@@ -639,11 +674,12 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
         const int tx = tid % 16, ty = tid / 16;
         const size_t npx = (size_t)nx * ny;
         const float k2 = a.k2;
-        float dsq = 0.f, nsq = 0.f;
         bool bad = false, ok = true;
         int kk = 0;
-        for (int t = t0, u = 0; t < t1 && ok; t += tstep, ++u) {
+        for (int q = t0, u = 0; q < t1 && ok; q += tstep, ++u) {
             const int ub = u % kTmaUBufs;
+            const int t = q / split, half = q - t * split;
+            const int r0 = half ? RMID : 0, r1 = (split == 1 || half) ? W : RMID;
             const int tile = t / N, i = t % N;
             const int x0 = (tile % tilesx) * kTmaTW + 4 * tx, y = (tile / tilesx) * kTmaTH + ty;
             const bool rowin = x0 < nx && y < ny;
@@ -660,12 +696,12 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
             // window rows of this thread inside the neighbour tiles
             const float* Un = utile + ub * 2 * kTmaUFloats + (ty + 7) * kTmaUW + 4 * tx + 8 - UOFF;
             const float* Up = Un + kTmaUFloats;
-            if (!mbar_wait_bounded(&ufull[ub], (unsigned)((u / kTmaUBufs) & 1))) {
+            const bool uok = mbar_wait_bounded(&ufull[ub], (unsigned)((u / kTmaUBufs) & 1), wlim);
+            if (!uok) {
                 s_abort = 1;
-                ok = false;
-                break;
+                ok = false;     // skips the window loop; the unit ends at the vote below
             }
-            for (int sy = 0; sy < W && ok; ++sy) {
+            for (int sy = r0; sy < r1 && ok; ++sy) {
                 const int dy = sy - RHO;
                 // window rows as float4 chunks, loaded when the sliding window
                 // first reaches them (forward slides right, backward left), so
@@ -677,7 +713,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
                 for (int sx = 0; sx < W; ++sx, ++kk) {
                     const int dx = sx - RHO;
                     const int slot = kk % kTmaStages;
-                    if (!mbar_wait_bounded(&full[slot], (unsigned)((kk / kTmaStages) & 1))) {
+                    if (!mbar_wait_bounded(&full[slot], (unsigned)((kk / kTmaStages) & 1), wlim)) {
                         s_abort = 1;
                         ok = false;
                         break;
@@ -718,8 +754,32 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&uempty[ub]);   // this warp is done with the tile's windows
-            if (!ok) break;
+            // this warp is done with the tile's windows (a buffer whose load
+            // was never seen complete is not handed back to the producer)
+            if (lane == 0 && uok) mbar_arrive(&uempty[ub]);
+            if (consumer_sync_or(!ok || *(volatile int*)&s_abort)) break;   // all consumers stop together
+            if (split > 1) {
+                float4* mine = hsum + ((size_t)t * 2 + half) * 4 * kTmaConsumers + tid;
+                mine[0] = make_float4(af[0], af[1], af[2], af[3]);
+                mine[kTmaConsumers] = make_float4(zf[0], zf[1], zf[2], zf[3]);
+                mine[2 * kTmaConsumers] = make_float4(ab[0], ab[1], ab[2], ab[3]);
+                mine[3 * kTmaConsumers] = make_float4(zb[0], zb[1], zb[2], zb[3]);
+                __threadfence();
+                consumer_sync();
+                if (tid == 0) s_second = atomicAdd(&hcnt[t], 1);
+                consumer_sync();
+                if (s_second == 0) continue;      // the other half finishes this tile
+                __threadfence();
+                const float4* oth = hsum + ((size_t)t * 2 + (1 - half)) * 4 * kTmaConsumers + tid;
+                const float4 o0 = __ldcg(oth), o1 = __ldcg(oth + kTmaConsumers);
+                const float4 o2 = __ldcg(oth + 2 * kTmaConsumers), o3 = __ldcg(oth + 3 * kTmaConsumers);
+                af[0] += o0.x; af[1] += o0.y; af[2] += o0.z; af[3] += o0.w;
+                zf[0] += o1.x; zf[1] += o1.y; zf[2] += o1.z; zf[3] += o1.w;
+                ab[0] += o2.x; ab[1] += o2.y; ab[2] += o2.z; ab[3] += o2.w;
+                zb[0] += o3.x; zb[1] += o3.y; zb[2] += o3.z; zb[3] += o3.w;
+                if (tid == 0) hcnt[t] = 0;        // ready for the next sweep
+            }
+            float dsq = 0.f, nsq = 0.f;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const int x = x0 + p;
@@ -737,15 +797,26 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
                     nsq = fmaf(fnew, fnew, nsq);
                 }
             }
-        }
-        if (bad) atomicOr(a.err, 8);
-        if (MODE == 1) {
-            const float d = warp_sum(dsq), n = warp_sum(nsq);
-            if (lane == 0) {
-                wsum[0][warp] = (double)d;
-                wsum[1][warp] = (double)n;
+            if (MODE == 1) {     // relative-change partials of this (tile, phase)
+                const float d = warp_sum(dsq), n = warp_sum(nsq);
+                if (lane == 0) {
+                    wsum[0][warp] = (double)d;
+                    wsum[1][warp] = (double)n;
+                }
+                consumer_sync();
+                if (tid == 0) {
+                    double d2 = 0.0, n2 = 0.0;
+                    for (int w = 0; w < kTmaConsumers / 32; ++w) {
+                        d2 += wsum[0][w];
+                        n2 += wsum[1][w];
+                    }
+                    a.part[2 * (size_t)t] = d2;
+                    a.part[2 * (size_t)t + 1] = n2;
+                }
+                consumer_sync();
             }
         }
+        if (bad) atomicOr(a.err, 8);
     }
     __syncthreads();
     if (s_abort) {
@@ -760,15 +831,6 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
         }
         __syncthreads();
         return;
-    }
-    if (MODE == 1 && tid == 0) {
-        double d2 = 0.0, n2 = 0.0;
-        for (int w = 0; w < kTmaConsumers / 32; ++w) {
-            d2 += wsum[0][w];
-            n2 += wsum[1][w];
-        }
-        a.part[2 * (size_t)blockIdx.x] = d2;
-        a.part[2 * (size_t)blockIdx.x + 1] = n2;
     }
 }
 
@@ -801,13 +863,31 @@ static cudaError_t prepare_gj_tma(int* slots) {
     return cudaSuccess;
 }
 
+long g_gj_wait_limit = kSpinLimit;
+
 // Tiles per CTA of the TMA sweep: one unless the autotuner measured more to
 // be faster on this device and shape.
 static int gj_tma_tpb(const tnlm_geometry* g) { return g->tune_gj_tpb > 0 ? g->tune_gj_tpb : 1; }
+static int gj_tma_tiles(const tnlm_geometry* g) {
+    return ((g->nx + kTmaTW - 1) / kTmaTW) * ((g->ny + kTmaTH - 1) / kTmaTH) * g->N;
+}
+// Halves of the window per (tile, phase): 2 when that fills the device's
+// resident CTA slots in whole waves clearly better (fraction of the last
+// wave that is busy), e.g. 640 (tile, phase) pairs on 456 slots.
+int gj_tma_split(const tnlm_geometry* g) {
+    if (g->tune_gj_split > 0) return g->tune_gj_split;
+    const double slots = g->cta_slots_gj > 0 ? g->cta_slots_gj : 1;
+    auto fill = [&](double units) { return units / (slots * ceil(units / slots)); };
+    const double t = gj_tma_tiles(g);
+    return fill(2 * t) > fill(t) + 0.1 ? 2 : 1;
+}
 static int gj_tma_blocks(const tnlm_geometry* g) {
-    const int tiles = ((g->nx + kTmaTW - 1) / kTmaTW) * ((g->ny + kTmaTH - 1) / kTmaTH) * g->N;
+    const int units = gj_tma_tiles(g) * gj_tma_split(g);
     const int tpb = gj_tma_tpb(g);
-    return (tiles + tpb - 1) / tpb;
+    return (units + tpb - 1) / tpb;
+}
+size_t gj_split_floats(const tnlm_geometry* g) {
+    return (size_t)gj_tma_tiles(g) * 2 * 4 * kTmaConsumers * 4;
 }
 
 template <int MODE>
@@ -816,15 +896,16 @@ static bool launch_gj_tma(const tnlm_geometry* g, const GjArgs& a, const Workspa
     const size_t sm = tma_smem();
     const CUtensorMap* U = a.uin == ws.U0 ? &ws.tmU0 : (a.uin == ws.U1 ? &ws.tmU1 : nullptr);
     if (!U) return false;
-    const int nb = gj_tma_blocks(g), tpb = gj_tma_tpb(g);
+    const int nb = gj_tma_blocks(g), tpb = gj_tma_tpb(g), sp = gj_tma_split(g);
+    float4* hs = (float4*)ws.gjsum;
     switch (window) {
-        case 3: k_gj_tma<3, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
-        case 5: k_gj_tma<5, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
-        case 7: k_gj_tma<7, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
-        case 9: k_gj_tma<9, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
-        case 11: k_gj_tma<11, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
-        case 13: k_gj_tma<13, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
-        case 15: k_gj_tma<15, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb); return true;
+        case 3: k_gj_tma<3, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb, sp, hs, ws.gjcnt, g_gj_wait_limit); return true;
+        case 5: k_gj_tma<5, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb, sp, hs, ws.gjcnt, g_gj_wait_limit); return true;
+        case 7: k_gj_tma<7, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb, sp, hs, ws.gjcnt, g_gj_wait_limit); return true;
+        case 9: k_gj_tma<9, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb, sp, hs, ws.gjcnt, g_gj_wait_limit); return true;
+        case 11: k_gj_tma<11, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb, sp, hs, ws.gjcnt, g_gj_wait_limit); return true;
+        case 13: k_gj_tma<13, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb, sp, hs, ws.gjcnt, g_gj_wait_limit); return true;
+        case 15: k_gj_tma<15, MODE><<<nb, kTmaThreads, sm, st>>>(a, ws.tmF, ws.tmB, *U, tpb, sp, hs, ws.gjcnt, g_gj_wait_limit); return true;
         default: return false;
     }
 }
@@ -928,7 +1009,7 @@ cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int win
                            ws.pp.py >= ty16 + 2 * ws.pp.oy;
     if (layout_ok && ws.tm_ok &&
         (fout ? launch_gj_tma<1>(g, a, ws, window, st) : launch_gj_tma<0>(g, a, ws, window, st))) {
-        const int nt = gj_tma_blocks(g), nmax = ns > nv ? ns : nv;
+        const int nt = gj_tma_tiles(g), nmax = ns > nv ? ns : nv;
         if (fout && nmax > nt) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nt, 0, 16 * (size_t)(nmax - nt), st);
         return cudaGetLastError();
     }

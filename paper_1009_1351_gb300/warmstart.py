@@ -20,7 +20,10 @@ FBP of all views, box step 1) and decides the result.
 2. Training: mean squared error, Adam, images scaled by 50 (unit order).
 3. Evaluation on held-out seeds: iterations to the stopping tolerance
    (relative change of f below tol), device time and the error of the final
-   image, from the usual start (cold) and from the network (warm).
+   image, from the usual start (cold) and from the network (warm); then the
+   batched + warm-started form (network starts, one batched launch per
+   chunk of slices, each slice stopping at the same rule) against the plain
+   GPU form (one call per slice from the usual start).
 """
 from __future__ import annotations
 
@@ -153,6 +156,8 @@ def evaluate(torch, tn, net, maker: PairMaker, data, tol: float, kmax: int):
         p = synth.Params(**{**c.params.__dict__, "k_outer": kmax})
         import types
         pt = types.SimpleNamespace(**p.__dict__, tol=tol, tol_check_every=1)
+        data.setdefault("y", {})[i] = y
+        data.setdefault("lam", {})[i] = lam
         res = {}
         for mode in ("cold", "warm"):
             if mode == "cold":
@@ -169,6 +174,7 @@ def evaluate(torch, tn, net, maker: PairMaker, data, tol: float, kmax: int):
             e1.record()
             e1.synchronize()
             res[mode] = (f, rep["iterations"], e0.elapsed_time(e1))
+        data.setdefault("cold_result", {})[i] = res["cold"][0]
         fc, fw = res["cold"][0].double(), res["warm"][0].double()
         t = truth.double()
         rows.append({"scenario": sc, "seed": sd,
@@ -178,6 +184,72 @@ def evaluate(torch, tn, net, maker: PairMaker, data, tol: float, kmax: int):
                      "err_truth_warm": float((fw - t).norm() / t.norm()),
                      "warm_vs_cold": float((fw - fc).norm() / fc.norm())})
     return rows
+
+
+def warm_start(torch, net, inp, batch: int = 8):
+    """Network start images for a list of per-phase FBP stacks."""
+    out = []
+    for b in range(0, len(inp), batch):
+        x = torch.stack(inp[b:b + batch]) * SCALE
+        o = torch.empty_like(x)
+        net.forward(x, o)
+        out.extend(torch.clamp(o / SCALE, min=0.0).unbind(0))
+    return [t.contiguous() for t in out]
+
+
+def evaluate_batched(torch, tn, net, maker: PairMaker, data, tol: float, kmax: int, chunk: int = 64):
+    """The batched + warm-started form against the plain GPU form on the
+    held-out slices (after evaluate(), which keeps their sinograms and cold
+    results): chunks of slices of all scenarios, network start images, then
+    ONE tnlm_reconstruct_batch launch per chunk in which every slice stops
+    at the same rule as a single cold call (tol, checked every iteration).
+    The plain form's time is the sum of the single cold calls' device
+    times; the batched cold form (all-views FBP starts) separates the two
+    gains."""
+    import types
+    n = len(data["seed"])
+    pool: Dict[str, List[object]] = {s: [] for s in SCENARIOS}
+    tot = {"batched_cold_ms": 0.0, "batched_warm_ms": 0.0}
+    iters = {"batched_cold": [], "batched_warm": []}
+    err_truth, vs_cold = [], []
+    for c0 in range(0, n, chunk):
+        idx = list(range(c0, min(n, c0 + chunk)))
+        used = {s: 0 for s in SCENARIOS}
+        geos, ps = [], []
+        for i in idx:
+            sc = data["scenario"][i]
+            if used[sc] == len(pool[sc]):
+                pool[sc].append(tn.tnlm_create_geometry(maker.cases[sc].geom))
+            geos.append(pool[sc][used[sc]])
+            used[sc] += 1
+            p = synth.Params(**{**maker.cases[sc].params.__dict__, "k_outer": kmax})
+            ps.append(types.SimpleNamespace(**p.__dict__, tol=tol, tol_check_every=1))
+        ys = [data["y"][i] for i in idx]
+        lams = [data["lam"][i] for i in idx]
+        for mode in ("batched_cold", "batched_warm"):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            if mode == "batched_cold":
+                fs = [data["init"][i].clone() for i in idx]
+            torch.cuda.synchronize()
+            e0.record()
+            if mode == "batched_warm":
+                fs = warm_start(torch, net, [data["inp"][i] for i in idx])
+            reps = tn.tnlm_reconstruct_batch(geos, ps, ys, lams, fs, autotune=False)
+            e1.record()
+            e1.synchronize()
+            tot[mode + "_ms"] += e0.elapsed_time(e1)
+            iters[mode] += [r["iterations"] for r in reps]
+        for i, f in zip(idx, fs):
+            t = data["truth"][i].double()
+            fc = data["cold_result"][i].double()
+            err_truth.append(float((f.double() - t).norm() / t.norm()))
+            vs_cold.append(float((f.double() - fc).norm() / fc.norm()))
+    return {"slices": n, "chunk": chunk, "loop_graph": tn.tnlm_batch_last_was_loop(),
+            "batched_cold_ms": tot["batched_cold_ms"], "batched_warm_ms": tot["batched_warm_ms"],
+            "iters_batched_cold": float(np.mean(iters["batched_cold"])),
+            "iters_batched_warm": float(np.mean(iters["batched_warm"])),
+            "err_truth_batched_warm": float(np.mean(err_truth)),
+            "batched_warm_vs_single_cold": float(np.mean(vs_cold))}
 
 
 def time_net(torch, tn, base: int, levels: int, batch: int, reps: int = 10) -> Dict[str, float]:
@@ -225,6 +297,7 @@ def main() -> None:
     ap.add_argument("--base", type=int, default=32)
     ap.add_argument("--levels", type=int, default=4)
     ap.add_argument("--seed", type=int, default=7000)
+    ap.add_argument("--chunk", type=int, default=64, help="slices per batched launch in the evaluation")
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
     torch.cuda.set_device(0)
@@ -276,6 +349,10 @@ def main() -> None:
     summ = {k: float(np.mean([r[k] for r in rows])) for k in
             ("iters_cold", "iters_warm", "ms_cold", "ms_warm", "err_truth_cold", "err_truth_warm",
              "warm_vs_cold")}
+    bat = evaluate_batched(torch, tn, net, maker, test, args.tol, args.kmax, args.chunk)
+    bat["plain_ms"] = float(np.sum([r["ms_cold"] for r in rows]))
+    bat["speedup_batched_warm_vs_plain"] = bat["plain_ms"] / bat["batched_warm_ms"]
+    bat["speedup_batched_cold_vs_plain"] = bat["plain_ms"] / bat["batched_cold_ms"]
     ti = train.get("target_iters", [])
     out = {"train": args.train, "test": args.test, "epochs": args.epochs, "batch": args.batch,
            "target": (f"TNLM to tol {args.target_tol} (mean {np.mean(ti):.1f} iterations)" if ti
@@ -283,7 +360,7 @@ def main() -> None:
            "net": {"base": args.base, "levels": args.levels, "params": net.param_count},
            "seconds": {"data": round(t_data, 1), "train": round(t_train, 1)},
            "loss": hist, "identity_test_loss": base_loss, "tol": args.tol,
-           "mean": summ, "per_slice": rows}
+           "mean": summ, "batched": bat, "per_slice": rows}
     print(json.dumps({k: v for k, v in out.items() if k != "per_slice"}))
     if args.out:
         with open(args.out, "w") as fh:

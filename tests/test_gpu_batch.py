@@ -1,7 +1,7 @@
 """Batched reconstruction and the launch autotuner (GPU, through the C ABI).
 
 A batch must give every slice bitwise the result of its own
-tnlm_reconstruct call.  The autotuner's sweep tiling leaves results bitwise
+tnlm_reconstruct call, including where it stops under its own tolerance.  The autotuner's sweep tiling leaves results bitwise
 unchanged; its choice of backprojection view groups reorders FP32 sums, so
 results after it agree with the default to rounding (rel. L2 <= 1e-6).  One
 slice of the batch is also checked against the FP64 oracle.
@@ -51,7 +51,10 @@ def inputs(c):
     return d, f0
 
 
-def test_batch_matches_single_calls_bitwise(tn):
+def test_batch_replays_match_single_calls_bitwise(tn, monkeypatch):
+    """The replay path (one graph of one outer iteration of the live slices,
+    launched once per iteration) gives every slice its single-call result."""
+    monkeypatch.setenv("TNLM_BATCH_REPLAY", "1")
     cases = small_slices()
     geoms, ys, ws, fs, ref = [], [], [], [], []
     for c in cases:
@@ -66,7 +69,7 @@ def test_batch_matches_single_calls_bitwise(tn):
         fs.append(dev(f0))
     reps = tn.tnlm_reconstruct_batch(geoms, [c.params for c in cases], ys, ws, fs, autotune=False)
     torch.cuda.synchronize()
-    assert not tn.tnlm_batch_last_was_loop()          # uneven K: per-iteration replays
+    assert not tn.tnlm_batch_last_was_loop()
     for c, f, (fr, rr), r in zip(cases, fs, ref, reps):
         assert torch.equal(f, fr), c.name
         assert r["iterations"] == c.params.k_outer
@@ -81,29 +84,69 @@ def test_batch_matches_single_calls_bitwise(tn):
         assert torch.equal(f1, f2), c.name
 
 
-def test_equal_k_batch_runs_as_one_loop_graph_and_matches_single_calls(tn):
-    """With one K for every slice the whole run is one graph launch (a
-    device-side WHILE loop around one outer iteration of all slices); the
-    results are still bitwise those of separate calls."""
-    cases = [synth.Case(c.name, c.geom, synth.Params(**{**c.params.__dict__, "k_outer": 3}), c.i0, c.seed,
-                        c.with_spine_diaphragm) for c in small_slices()]
-    geoms, ys, ws, fs, ref = [], [], [], [], []
-    for c in cases:
+def run_pair(tn, cases, plist):
+    """Single tnlm_reconstruct calls and one batched call on the same inputs."""
+    geoms, ys, ws, fs, ref, ref_it = [], [], [], [], [], []
+    for c, p in zip(cases, plist):
         d, f0 = inputs(c)
         g = tn.tnlm_create_geometry(c.geom)
         f = dev(f0)
-        tn.tnlm_reconstruct(g, c.params, dev(d["y"]), dev(d["w"]), f)
+        rep = tn.tnlm_reconstruct(g, p, dev(d["y"]), dev(d["w"]), f)
         ref.append(f)
+        ref_it.append(rep["iterations"])
         geoms.append(tn.tnlm_create_geometry(c.geom))
         ys.append(dev(d["y"])); ws.append(dev(d["w"])); fs.append(dev(f0))
-    for rep in range(2):      # the second call replays the cached loop graph
+    return geoms, ys, ws, fs, ref, ref_it
+
+
+def test_batch_runs_as_one_loop_graph_and_matches_single_calls(tn):
+    """Uneven iteration counts: the whole run is one graph launch (a
+    device-side WHILE loop whose gate runs each slice's iteration while it
+    has one left); the results are bitwise those of separate calls, also
+    when the cached loop graph is launched again."""
+    cases = small_slices()
+    plist = [c.params for c in cases]
+    assert len({p.k_outer for p in plist}) > 1
+    geoms, ys, ws, fs, ref, ref_it = run_pair(tn, cases, plist)
+    for rep in range(2):
         fr = [f.clone() for f in fs]
-        reps = tn.tnlm_reconstruct_batch(geoms, [c.params for c in cases], ys, ws, fr, autotune=False)
+        reps = tn.tnlm_reconstruct_batch(geoms, plist, ys, ws, fr, autotune=False)
         torch.cuda.synchronize()
         assert tn.tnlm_batch_last_was_loop()
         for c, f, r, rp in zip(cases, fr, ref, reps):
             assert torch.equal(f, r), (rep, c.name)
-            assert rp["iterations"] == 3
+            assert rp["iterations"] == c.params.k_outer
+
+
+def tol_params(cases, rules):
+    import types
+    return [types.SimpleNamespace(**{**c.params.__dict__, "k_outer": k, "tol": tol, "tol_check_every": ev})
+            for c, (k, tol, ev) in zip(cases, rules)]
+
+
+@pytest.mark.parametrize("replay", [False, True])
+def test_batch_stops_each_slice_at_its_tolerance(tn, monkeypatch, replay):
+    """Every slice its own stopping rule (tolerance, check interval, cap):
+    the batched launch (gate on the device; or, replaying, checks on the
+    host) stops each slice at the iteration where its own tnlm_reconstruct
+    call stops, with bitwise the same image.  A second call with other
+    tolerances reuses the cached loop graph (the rules live in device
+    memory, not in the graph)."""
+    if replay:
+        monkeypatch.setenv("TNLM_BATCH_REPLAY", "1")
+    cases = small_slices()
+    for rules in ([(12, 0.03, 1), (12, 0.01, 2), (7, 0.0, 1), (12, 0.05, 3)],
+                  [(12, 0.015, 1), (12, 0.02, 2), (9, 0.0, 1), (12, 0.03, 2)]):
+        plist = tol_params(cases, rules)
+        geoms, ys, ws, fs, ref, ref_it = run_pair(tn, cases, plist)
+        assert any(it < p.k_outer for it, p in zip(ref_it, plist))   # some tolerance fired
+        assert len(set(ref_it)) > 1
+        reps = tn.tnlm_reconstruct_batch(geoms, plist, ys, ws, fs, autotune=False)
+        torch.cuda.synchronize()
+        assert tn.tnlm_batch_last_was_loop() != replay
+        for c, f, r, it, rp in zip(cases, fs, ref, ref_it, reps):
+            assert rp["iterations"] == it, (c.name, rp["iterations"], it)
+            assert torch.equal(f, r), c.name
 
 
 def test_batch_slice_matches_oracle(tn, oracle_mod):
@@ -147,22 +190,15 @@ def test_autotune_choices_leave_results_unchanged(tn):
     assert tn.tnlm_autotune(g2, p, y, w, f0) == choice
 
 
-def test_batch_rejects_tolerance_and_repeated_handles(tn):
-    import types
+def test_batch_rejects_repeated_handles(tn):
     c = small_slices()[0]
     d, f0 = inputs(c)
     g = tn.tnlm_create_geometry(c.geom)
-    g2 = tn.tnlm_create_geometry(c.geom)
     y, w, f = dev(d["y"]), dev(d["w"]), dev(f0)
     with pytest.raises(tn.TnlmError) as e:
         tn.tnlm_reconstruct_batch([g, g], [c.params, c.params], [y, y], [w, w], [f, f.clone()])
     assert e.value.status == tn.TNLM_ERR_INVALID_ARG
     assert "repeats" in str(e.value)
-    p_tol = types.SimpleNamespace(**c.params.__dict__, tol=1e-3, tol_check_every=1)
-    with pytest.raises(tn.TnlmError) as e:
-        tn.tnlm_reconstruct_batch([g, g2], [c.params, p_tol], [y, y], [w, w], [f, f.clone()])
-    assert e.value.status == tn.TNLM_ERR_INVALID_ARG
-    assert "tol" in str(e.value)
     assert torch.equal(f, dev(f0))                     # nothing ran
 
 

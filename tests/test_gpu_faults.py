@@ -1,6 +1,8 @@
 """Failure handling of the C ABI on a GPU, all provoked from the host:
-bad arguments, an injected allocation failure, non-finite inputs.  No test
-here makes a kernel fault, trap or wait."""
+bad arguments, an injected allocation failure, non-finite inputs, and a
+pipeline wait of the TMA sweep that runs out (its poll limit lowered to
+zero, so no wait blocks at all).  No test here makes a kernel fault, trap
+or hang."""
 import numpy as np
 import pytest
 
@@ -100,3 +102,32 @@ def test_nonfinite_input_raises_numeric(tn, case):
     assert e.value.status == tn.TNLM_ERR_NUMERIC
     # the flag is cleared once reported
     tn.tnlm_reconstruct(geo, p, y, w, f0.clone())
+
+
+def test_sweep_wait_timeout_is_reported_and_the_handle_recovers(tn, case):
+    """With the sweep's pipeline waits limited to zero polls every wait gives
+    up at once: the sweep blocks stop issuing copies, drain the ones in
+    flight (with the normal limit) and flag a timeout, which the
+    synchronising call reports as TNLM_ERR_TIMEOUT.  With the limit restored
+    the same handle reconstructs exactly as a fresh one."""
+    c, y, w, f0 = case
+    p = synth.Params(**{**c.params.__dict__, "k_outer": 1})   # eager launches, no captured graph
+    geo = tn.tnlm_create_geometry(c.geom)
+    f = f0.clone()
+    tn.tnlm_debug_wait_limit(0)
+    try:
+        with pytest.raises(tn.TnlmError) as e:
+            tn.tnlm_reconstruct(geo, p, y, w, f)
+    finally:
+        tn.tnlm_debug_wait_limit(-1)
+    assert e.value.status == tn.TNLM_ERR_TIMEOUT
+    assert "timed out" in str(e.value)
+    torch.cuda.synchronize()
+    a = f0.clone()
+    rep = tn.tnlm_reconstruct(geo, p, y, w, a)
+    fresh = tn.tnlm_create_geometry(c.geom)
+    b = f0.clone()
+    tn.tnlm_reconstruct(fresh, p, y, w, b)
+    torch.cuda.synchronize()
+    assert rep["iterations"] == 1
+    assert torch.equal(a, b)

@@ -161,11 +161,15 @@ def normalised_from_gpu(D, norm, W, h):
 
 
 @pytest.mark.parametrize("shape,d,W", [((4, 21, 35), 3, 5), ((3, 40, 70), 5, 11),
-                                       ((3, 37, 45), 7, 15), ((5, 17, 33), 1, 3)])
+                                       ((3, 37, 45), 7, 15), ((5, 17, 33), 1, 3),
+                                       ((3, 512, 512), 5, 11)])
 def test_weights_match_oracle(tn, oracle_mod, shape, d, W):
+    """Small shapes split each tile's shifts over several CTAs (minima
+    combined by atomic min); 512 x 512 x 3 has enough tiles for one CTA per
+    tile and phase."""
     N, ny, nx = shape
-    geom = synth.Geometry(nx=nx, ny=ny, pixel_mm=1.0, n_phases=N, n_views=4, n_bins=16,
-                          bin_mm=1.0, sid_mm=500.0, sdd_mm=800.0)
+    geom = synth.Geometry(nx=nx, ny=ny, pixel_mm=min(1.0, 128.0 / max(nx, ny)), n_phases=N, n_views=4,
+                          n_bins=16, bin_mm=1.0, sid_mm=500.0, sdd_mm=800.0)
     geo = tn.tnlm_create_geometry(geom)
     rng = np.random.default_rng(10 + d)
     base = 0.02 * rng.random((ny, nx))
