@@ -1,0 +1,78 @@
+"""Writes the stored expected values under tests/golden/ from the FP64
+oracle alone (test infrastructure: nothing here touches the CUDA path).
+
+    python tests/golden/make_golden.py
+
+tiny_k3.txt: the tiny workload (64 x 64 pixels of 1 mm, 10 phases, 60 views
+per phase, 128 bins of 1.2 mm, SID 1000 / SDD 1500 mm, I0 = 1e4, d = 3,
+W = 5, h = 0.006, mu_hat = 0.5, M1 = 3 CGLS steps, M2 = 5 Gauss-Jacobi
+sweeps, clamp), three outer iterations of the TNLM algorithm box from the
+constant start image 0.01: the relative change and data residual after
+every iteration and 96 pixel values at seeded positions.
+"""
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+K = 3
+SAMPLES = 96
+SAMPLE_SEED = 3141
+
+
+def sample_positions(shape, n=SAMPLES, seed=SAMPLE_SEED):
+    """Seeded positions inside the body ellipse (central 60 % of each axis)."""
+    rng = np.random.default_rng(seed)
+    N, ny, nx = shape
+    return np.stack([rng.integers(0, N, n), rng.integers(ny // 5, ny - ny // 5, n),
+                     rng.integers(nx // 5, nx - nx // 5, n)], axis=1)
+
+
+def tiny_k3():
+    import oracle
+    from paper_1009_1351_gb300 import synth
+    c = synth.case("tiny")
+    d = synth.make_inputs(c)
+    p = synth.Params(**{**c.params.__dict__, "k_outer": K})
+    f0 = np.full((c.geom.n_phases, c.geom.ny, c.geom.nx), 0.01, np.float32)
+    f, rel, res = oracle.reconstruct(oracle.Geom(c.geom), d["y"].astype(np.float32),
+                                     d["w"].astype(np.float32), f0, p)
+    return f, np.asarray(rel), np.asarray(res)
+
+
+def write_tiny_k3(path=os.path.join(HERE, "tiny_k3.txt")):
+    f, rel, res = tiny_k3()
+    pos = sample_positions(f.shape)
+    with open(path, "w") as fh:
+        fh.write("# TNLM algorithm box, tiny workload, K = 3 from f0 = 0.01 (FP64 oracle).\n")
+        fh.write("# Written by tests/golden/make_golden.py; see its docstring for the workload.\n")
+        fh.write("# iter <k> <relative change> <data residual>\n")
+        fh.write("# pixel <phase> <row> <column> <value>\n")
+        for k in range(len(rel)):
+            fh.write(f"iter {k + 1} {float(rel[k])!r} {float(res[k])!r}\n")
+        for i, y, x in pos:
+            fh.write(f"pixel {i} {y} {x} {float(f[i, y, x])!r}\n")
+
+
+def read_tiny_k3(path=os.path.join(HERE, "tiny_k3.txt")):
+    iters, pix = [], []
+    for line in open(path):
+        t = line.split()
+        if not t or t[0].startswith("#"):
+            continue
+        if t[0] == "iter":
+            iters.append((int(t[1]), float(t[2]), float(t[3])))
+        elif t[0] == "pixel":
+            pix.append((int(t[1]), int(t[2]), int(t[3]), float(t[4])))
+    return iters, pix
+
+
+if __name__ == "__main__":
+    import oracle
+    oracle.build()
+    write_tiny_k3()
+    print("wrote", os.path.join(HERE, "tiny_k3.txt"))

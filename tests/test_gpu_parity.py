@@ -361,3 +361,23 @@ def test_fbp_initial_image_matches_oracle(tn, oracle_mod, name):
     got = host(out)
     assert rel_l2(got, ref) <= 2e-5
     assert all(np.array_equal(got[0], got[i]) for i in range(1, g.n_phases))
+
+
+def test_tiny_reconstruction_matches_the_stored_oracle_values(tn):
+    """The CUDA path against the stored FP64-oracle values of
+    tests/golden/tiny_k3.txt (no oracle run needed): sampled pixels within
+    relative L2 1e-4, the per-iteration monitors within 1e-4 relative."""
+    from tests.golden import make_golden
+    iters, pix = make_golden.read_tiny_k3()
+    c = synth.case("tiny")
+    d = synth.make_inputs(c)
+    p = synth.Params(**{**c.params.__dict__, "k_outer": make_golden.K})
+    geo = tn.tnlm_create_geometry(c.geom)
+    f = dev(np.full((c.geom.n_phases, c.geom.ny, c.geom.nx), 0.01))
+    rep = tn.tnlm_reconstruct(geo, p, dev(d["y"]), dev(d["w"]), f)
+    got_f = host(f)
+    got = np.array([got_f[i, y, x] for i, y, x, _ in pix])
+    want = np.array([v for _, _, _, v in pix])
+    assert rel_l2(got, want) <= REC_TOL
+    np.testing.assert_allclose(rep["rel_change_hist"], [r for _, r, _ in iters], rtol=1e-4)
+    np.testing.assert_allclose(rep["residual_hist"], [r for _, _, r in iters], rtol=1e-4)
