@@ -141,7 +141,10 @@ def roofline_units(case, cls: str):
         b = 4 * N * L2 * W2 + 4 * N * L2 * (2 + 2 + 1)
         return b, "GB/s", "hbm"
     if cls in ("project", "backproject"):
-        return 2.0 * system_nnz(g), "TFLOP/s", "alu"
+        # per non-zero of A (one segment update): 1 FMA + 6 ALU operations to form
+        # the entry (position, floor, fraction, row index, bounds), i.e. 7 lane
+        # operations of the FP32 pipe
+        return 7.0 * system_nnz(g), "Tops/s", "alu"
     return None, None, None
 
 
@@ -171,10 +174,11 @@ def measured_traffic(cls: str, case_names):
     return float(np.mean(vals))
 
 
-def fp32_peak_tflops():
-    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flop x max SM clock."""
+def alu_peak_tops():
+    """FP32-pipe peak: 152 SMs x 128 lanes x one operation per lane and clock
+    x max SM clock (an FMA counts as one operation, as in the per-nnz count)."""
     mhz = _peaks().get("sm_max_mhz", 2070.0)
-    return 152 * 128 * 2 * mhz * 1e6 / 1e12
+    return 152 * 128 * mhz * 1e6 / 1e12
 
 
 # ---------------------------------------------------------------------------
@@ -318,8 +322,8 @@ def run_gpu(args):
             else:
                 amt = np.mean([roofline_units(c, dominant)[0] for c in cases])
                 achieved = amt / (per_launch_ms / 1e3) / 1e12
-                peak = fp32_peak_tflops()
-                src = "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"
+                peak = alu_peak_tops()
+                src = "derived: 152 SMs x 128 FP32 lanes x max SM clock (1 op per lane and clock)"
             traffic = measured_traffic(dominant, SCENARIOS)
             roof = {"bound": bound, "kernel": dominant, "achieved": round(achieved, 3),
                     "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
@@ -337,7 +341,7 @@ def run_gpu(args):
             if unit_c == "GB/s":
                 ach, pk = amt_c / (ms_c / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0)
             else:
-                ach, pk = amt_c / (ms_c / 1e3) / 1e12, fp32_peak_tflops()
+                ach, pk = amt_c / (ms_c / 1e3) / 1e12, alu_peak_tops()
             tr = measured_traffic(cls, SCENARIOS)
             by_kernel[cls] = {"bound": bound_c, "achieved": round(ach, 3), "peak": round(pk, 1),
                               "unit": unit_c, "frac": round(ach / pk, 4), "launch_ms": round(ms_c, 4),
