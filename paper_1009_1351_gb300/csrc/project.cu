@@ -347,13 +347,30 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
             __syncwarp();
             myS[lane] = make_float4(rp.x, rp.y + fminf(rp.x, 0.f), rp.z, fabsf(rp.w) * zz);
             __syncwarp();
+            const unsigned staged = nb >= 32 ? full : (1u << nb) - 1u;
+            if (colmask == staged && ncols == kBpT) {
+                // the usual case: one class for the whole chunk, a full tile
+                // side of lanes -- no per-ray class or lane test
+#pragma unroll 4
+                for (int t = 0; t < nb; ++t) {
+                    const float4 r = myS[t];
+                    deposit(myC, r.x, r.y, r.z, r.w, kfc, Y0, (unsigned)nrows);
+                }
+            } else if (colmask == 0u && nrows == kBpT) {
+#pragma unroll 4
+                for (int t = 0; t < nb; ++t) {
+                    const float4 r = myS[t];
+                    deposit(myR, r.x, r.y, r.z, r.w, kfr, X0, (unsigned)ncols);
+                }
+            } else {
 #pragma unroll 2
-            for (int t = 0; t < nb; ++t) {
-                const float4 r = myS[t];
-                if ((colmask >> t) & 1u) {
-                    if (lane < ncols) deposit(myC, r.x, r.y, r.z, r.w, kfc, Y0, (unsigned)nrows);
-                } else {
-                    if (lane < nrows) deposit(myR, r.x, r.y, r.z, r.w, kfr, X0, (unsigned)ncols);
+                for (int t = 0; t < nb; ++t) {
+                    const float4 r = myS[t];
+                    if ((colmask >> t) & 1u) {
+                        if (lane < ncols) deposit(myC, r.x, r.y, r.z, r.w, kfc, Y0, (unsigned)nrows);
+                    } else {
+                        if (lane < nrows) deposit(myR, r.x, r.y, r.z, r.w, kfr, X0, (unsigned)ncols);
+                    }
                 }
             }
             if (nvi < 0) break;

@@ -979,8 +979,8 @@ static int gjs_blocks(const tnlm_geometry* g) {
     return ((g->nx + kGjTileX - 1) / kGjTileX) * ((g->ny + kGjTileY - 1) / kGjTileY) * g->N;
 }
 int gj_blocks(const tnlm_geometry* g) {
-    const int a = gjs_blocks(g), b = gjv_blocks(g);
-    return a > b ? a : b;
+    const int a = gjs_blocks(g), b = gjv_blocks(g), c = gj_tma_tiles(g);
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
 }
 
 static GjArgs gj_args(const tnlm_geometry* g, const Workspace& ws, int window, double h,
@@ -1071,18 +1071,30 @@ cudaError_t launch_finalize_nogj(const tnlm_geometry* g, const Workspace& ws, co
 }
 
 // Per-iteration monitors: relative change and the data term of f^(k-1).
-__global__ void k_iter_scalars(const double* part, int nblocks, const double* res0, int N,
-                               DevState st, int kcap) {
+// 256 threads so that each reads only a few partials (the loads, not the
+// FP64 adds, set the time); a fixed-order tree keeps the sum deterministic.
+constexpr int kScalThreads = 256;
+__global__ void __launch_bounds__(kScalThreads) k_iter_scalars(const double* part, int nblocks,
+                                                               const double* res0, int N, DevState st,
+                                                               int kcap) {
+    __shared__ double sd[kScalThreads], sn[kScalThreads];
     double d = 0.0, n = 0.0;
-    for (int k = threadIdx.x; k < nblocks; k += 32) {
+    for (int k = threadIdx.x; k < nblocks; k += kScalThreads) {
         d += part[2 * (size_t)k];
         n += part[2 * (size_t)k + 1];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        d += __shfl_down_sync(0xffffffffu, d, o);
-        n += __shfl_down_sync(0xffffffffu, n, o);
+    sd[threadIdx.x] = d;
+    sn[threadIdx.x] = n;
+    __syncthreads();
+    for (int h = kScalThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            sd[threadIdx.x] += sd[threadIdx.x + h];
+            sn[threadIdx.x] += sn[threadIdx.x + h];
+        }
+        __syncthreads();
     }
+    d = sd[0];
+    n = sn[0];
     if (threadIdx.x == 0) {
         double r = 0.0;
         for (int i = 0; i < N; ++i) r += res0[i];
@@ -1097,7 +1109,7 @@ __global__ void k_iter_scalars(const double* part, int nblocks, const double* re
 
 cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks,
                                 cudaStream_t st) {
-    k_iter_scalars<<<1, 32, 0, st>>>(ws.part2, nblocks, ws.st.res0, g->N, ws.st, ws.kcap);
+    k_iter_scalars<<<1, kScalThreads, 0, st>>>(ws.part2, nblocks, ws.st.res0, g->N, ws.st, ws.kcap);
     return cudaGetLastError();
 }
 
