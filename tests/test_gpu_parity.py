@@ -305,6 +305,29 @@ def test_mid_size_reconstruction_matches_oracle(tn, oracle_mod):
     assert rel_l2(got, ref) <= REC_TOL
 
 
+def test_bench_workload_slice_matches_oracle(tn, oracle_mod):
+    """The benchmark's 360-view slice (256^2, 10 phases, d = 5, W = 11) run
+    the way bench.py runs it -- the FBP of all views as the start image,
+    then the outer iterations through the captured graph -- for K = 5,
+    against the oracle run from its own FBP: the start images agree to
+    2e-5 and the reconstructions to relative L2 1e-4."""
+    c = synth.case("mid_a")
+    d = synth.make_inputs(c)
+    G = oracle_mod.Geom(c.geom)
+    y32, w32 = d["y"].astype(np.float32), d["w"].astype(np.float32)
+    geo = tn.tnlm_create_geometry(c.geom)
+    f = torch.zeros(G.img_shape, device="cuda")
+    tn.tnlm_fbp(geo, dev(y32), f)
+    f0_ref = oracle_mod.fbp(G, y32.astype(np.float64))
+    assert rel_l2(host(f), f0_ref) <= 2e-5
+    p = synth.Params(**{**c.params.__dict__, "k_outer": 5})
+    rep = tn.tnlm_reconstruct(geo, p, dev(y32), dev(w32), f)
+    ref, rel, res = oracle_mod.reconstruct(G, y32, w32, f0_ref.astype(np.float32), p)
+    assert rep["iterations"] == 5
+    assert rel_l2(host(f), ref) <= REC_TOL
+    np.testing.assert_allclose(rep["rel_change_hist"], rel, rtol=1e-3)
+
+
 def test_graph_replay_matches_eager_launches(tn, tiny_case):
     """With kernel timing on, iterations are launched one kernel at a time;
     otherwise a captured CUDA graph of one iteration is replayed.  Both must
