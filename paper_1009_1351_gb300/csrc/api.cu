@@ -273,8 +273,7 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     double* part_s = ws.part;
     double* part_i = ws.part + nps;
     // ---- data step: r0 = sqrt(w)(y - P f), s0 = P_n^T r0 (CGLS) / w(y - P f) back-projected (Eq. 4)
-    LK(TNLM_KCLASS_PREP, launch_prep_dual(g, d_f, ws.R, ws.T, st), "prep");
-    LK(TNLM_KCLASS_PREP, launch_copy(d_f, ws.u, (size_t)g->nx * g->ny * g->N, st), "copy");
+    LK(TNLM_KCLASS_PREP, launch_prep_dual_copy(g, d_f, ws.u, ws.R, ws.T, st), "prep");
     ProjOut o{};
     o.mode = 1; o.r = ws.r; o.z = ws.z; o.y = d_y; o.sw = ws.sw; o.part = part_s;
     LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, o, st), "project");
@@ -285,7 +284,14 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     } else {
         for (int m = 0; m < p->m1; ++m) {
             const bool last = m == p->m1 - 1;
-            LK(TNLM_KCLASS_PREP, launch_prep_dual(g, ws.s, ws.R, ws.T, st), "prep");
+            // from the second step on, the direction update s = P_n^T r + b s
+            // is fused into the layout preparation of s
+            if (m == 0)
+                LK(TNLM_KCLASS_PREP, launch_prep_dual(g, ws.s, ws.R, ws.T, st), "prep");
+            else
+                LK(TNLM_KCLASS_PREP,
+                   launch_prep_dual_update(g, ws.s, ws.gr, ws.st.b, ws.st.active, ws.R, ws.T, st),
+                   "cgls s + prep");
             ProjOut ot{};
             ot.mode = 2; ot.q = ws.t; ot.sw = ws.sw; ot.part = part_s;
             LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, ot, st), "project");
@@ -294,7 +300,6 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
             if (last) break;
             LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.gr, part_i, ws.bps, st), "backproject");
             LK(TNLM_KCLASS_CGLS, launch_cgls_b(g, ws, st), "cgls b");
-            LK(TNLM_KCLASS_CGLS, launch_cgls_update_s(g, ws, st), "cgls s");
         }
     }
     // ---- TNLM step: weights from g = ws.u, Gauss-Jacobi, positivity

@@ -11,14 +11,23 @@
 
 namespace tnlm {
 
-// Sum partials[base + 0 .. n) in a fixed order: lane-strided FP64 sums, then
-// an FP64 shuffle tree.  Called by one full warp; returns the total in lane 0.
-__device__ __forceinline__ double warp_sum_partials(const double* p, int n) {
+// Sum partials[0 .. n) in a fixed order: thread-strided FP64 sums, then an
+// FP64 tree over the block.  256 threads, so each thread loads only a few
+// partials (the dependent loads, not the adds, set the time).  Called by
+// the whole block; every thread returns the total.
+constexpr int kScalarThreads = 256;
+__device__ __forceinline__ double block_sum_partials(const double* p, int n, double* sh) {
     double s = 0.0;
-    for (int k = threadIdx.x; k < n; k += 32) s += p[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    return s;
+    for (int k = threadIdx.x; k < n; k += kScalarThreads) s += p[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = kScalarThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    const double t = sh[0];
+    __syncthreads();
+    return t;
 }
 
 struct ScalArgs {
@@ -30,10 +39,11 @@ struct ScalArgs {
 
 // After r^(0) = y_n - P_n u^(0) and s^(0) = P_n^T r^(0):
 // gamma = ||s^(0)||^2, res0 = ||r^(0)||^2, CGLS active.
-__global__ void k_cgls_init_scalars(ScalArgs a) {
+__global__ void __launch_bounds__(kScalarThreads) k_cgls_init_scalars(ScalArgs a) {
+    __shared__ double sh[kScalarThreads];
     const int i = blockIdx.x;
-    const double g = warp_sum_partials(a.part_i + (size_t)i * a.pi, a.pi);
-    const double r = warp_sum_partials(a.part_s + (size_t)i * a.ps, a.ps);
+    const double g = block_sum_partials(a.part_i + (size_t)i * a.pi, a.pi, sh);
+    const double r = block_sum_partials(a.part_s + (size_t)i * a.ps, a.ps, sh);
     if (threadIdx.x == 0) {
         a.st.gamma[i] = g;
         a.st.res0[i] = r;
@@ -43,9 +53,10 @@ __global__ void k_cgls_init_scalars(ScalArgs a) {
 }
 
 // Step 1: a = ||P_n^T r||^2 / ||P_n s||^2.
-__global__ void k_cgls_a(ScalArgs a) {
+__global__ void __launch_bounds__(kScalarThreads) k_cgls_a(ScalArgs a) {
+    __shared__ double sh[kScalarThreads];
     const int i = blockIdx.x;
-    const double den = warp_sum_partials(a.part_s + (size_t)i * a.ps, a.ps);
+    const double den = block_sum_partials(a.part_s + (size_t)i * a.ps, a.ps, sh);
     if (threadIdx.x == 0) {
         const double gam = a.st.gamma[i];
         if (!a.st.active[i] || den == 0.0 || gam == 0.0) {
@@ -59,9 +70,10 @@ __global__ void k_cgls_a(ScalArgs a) {
 }
 
 // Step 4: b = ||P_n^T r^(m+1)||^2 / ||P_n^T r^(m)||^2.
-__global__ void k_cgls_b(ScalArgs a) {
+__global__ void __launch_bounds__(kScalarThreads) k_cgls_b(ScalArgs a) {
+    __shared__ double sh[kScalarThreads];
     const int i = blockIdx.x;
-    const double gnew = warp_sum_partials(a.part_i + (size_t)i * a.pi, a.pi);
+    const double gnew = block_sum_partials(a.part_i + (size_t)i * a.pi, a.pi, sh);
     if (threadIdx.x == 0) {
         if (a.st.active[i]) {
             a.st.b[i] = gnew / a.st.gamma[i];
@@ -83,15 +95,15 @@ static ScalArgs scal_args(const tnlm_geometry* g, const Workspace& ws) {
 }
 
 cudaError_t launch_cgls_init_scalars(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st) {
-    k_cgls_init_scalars<<<g->N, 32, 0, st>>>(scal_args(g, ws));
+    k_cgls_init_scalars<<<g->N, kScalarThreads, 0, st>>>(scal_args(g, ws));
     return cudaGetLastError();
 }
 cudaError_t launch_cgls_a(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st) {
-    k_cgls_a<<<g->N, 32, 0, st>>>(scal_args(g, ws));
+    k_cgls_a<<<g->N, kScalarThreads, 0, st>>>(scal_args(g, ws));
     return cudaGetLastError();
 }
 cudaError_t launch_cgls_b(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st) {
-    k_cgls_b<<<g->N, 32, 0, st>>>(scal_args(g, ws));
+    k_cgls_b<<<g->N, kScalarThreads, 0, st>>>(scal_args(g, ws));
     return cudaGetLastError();
 }
 
@@ -138,26 +150,8 @@ cudaError_t launch_cgls_update_ur(const tnlm_geometry* g, const Workspace& ws, b
     return cudaGetLastError();
 }
 
-// Step 5: s = P_n^T r^(m+1) + b s.
-__global__ void __launch_bounds__(256) k_cgls_update_s(float* __restrict__ s,
-                                                       const float* __restrict__ gr,
-                                                       const double* __restrict__ bcoef,
-                                                       const int* __restrict__ active,
-                                                       size_t npx, int N) {
-    const size_t n = npx * N;
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
-        const int i = (int)(k / npx);
-        if (active[i]) s[k] = fmaf((float)bcoef[i], s[k], gr[k]);
-    }
-}
-
-cudaError_t launch_cgls_update_s(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st) {
-    const size_t npx = (size_t)g->nx * g->ny;
-    k_cgls_update_s<<<grid_for(npx * g->N), 256, 0, st>>>(ws.s, ws.gr, ws.st.b, ws.st.active,
-                                                          npx, g->N);
-    return cudaGetLastError();
-}
+// Step 5 (s = P_n^T r^(m+1) + b s) is fused into the layout preparation of
+// s for the next projection (k_prep_dual<2>, project.cu).
 
 // Eq. 4 with s = P^T w (y - P f) already formed: g = f + s / beta.
 __global__ void __launch_bounds__(256) k_grad_final(float* __restrict__ u,
@@ -192,17 +186,6 @@ __global__ void __launch_bounds__(256) k_sqrt(const float* __restrict__ w, float
 
 cudaError_t launch_sqrt(const float* w, float* sw, size_t n, int* err, cudaStream_t st) {
     k_sqrt<<<grid_for(n), 256, 0, st>>>(w, sw, n, err);
-    return cudaGetLastError();
-}
-
-__global__ void __launch_bounds__(256) k_copy(const float* __restrict__ s, float* __restrict__ d,
-                                              size_t n) {
-    const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) d[k] = s[k];
-}
-
-cudaError_t launch_copy(const float* src, float* dst, size_t n, cudaStream_t st) {
-    k_copy<<<grid_for(n), 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
 }
 

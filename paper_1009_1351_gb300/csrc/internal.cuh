@@ -128,6 +128,11 @@ struct ProjOut {
 int proj_chunks(const tnlm_geometry* g);
 cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R, float* T,
                              cudaStream_t st);
+cudaError_t launch_prep_dual_copy(const tnlm_geometry* g, const float* img, float* cp, float* R,
+                                  float* T, cudaStream_t st);
+cudaError_t launch_prep_dual_update(const tnlm_geometry* g, float* s, const float* gr,
+                                    const double* bcoef, const int* active, float* R, float* T,
+                                    cudaStream_t st);
 cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
                            const ProjOut& o, cudaStream_t st);
 cudaError_t prepare_backproject(int* slots);
@@ -158,11 +163,9 @@ cudaError_t launch_cgls_a(const tnlm_geometry* g, const Workspace& ws, cudaStrea
 cudaError_t launch_cgls_update_ur(const tnlm_geometry* g, const Workspace& ws, bool with_r,
                                   cudaStream_t st);
 cudaError_t launch_cgls_b(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st);
-cudaError_t launch_cgls_update_s(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st);
 cudaError_t launch_grad_final(const tnlm_geometry* g, const Workspace& ws, double beta,
                               cudaStream_t st);
 cudaError_t launch_sqrt(const float* w, float* sw, size_t n, int* err, cudaStream_t st);
-cudaError_t launch_copy(const float* src, float* dst, size_t n, cudaStream_t st);
 cudaError_t launch_fill(float* p, float v, size_t n, cudaStream_t st);
 
 // TNLM step kernels

@@ -43,21 +43,36 @@ namespace tnlm {
 // T[i][ix][iy+2] (column-major, two zero rows each side).  Pads are zeroed
 // once when the workspace is created and never written.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_prep_dual(const float* __restrict__ img,
-                                                   float* __restrict__ R, float* __restrict__ T,
-                                                   int nx, int ny) {
+// MODE 0: R, T of img.  MODE 1: also a copy of img into cp (u^(0) = f).
+// MODE 2: first the CGLS direction update img = gr + b_i img (for phases
+// whose CGLS is still active; the same FP32 operation as a separate update
+// kernel would do), written back, then R, T of the result.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_prep_dual(float* __restrict__ img, float* __restrict__ R,
+                                                   float* __restrict__ T, float* __restrict__ cp,
+                                                   const float* __restrict__ gr,
+                                                   const double* __restrict__ bcoef,
+                                                   const int* __restrict__ active, int nx, int ny) {
     __shared__ float tile[32][33];
     const int i = blockIdx.z;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
     const size_t npx = (size_t)nx * ny;
-    const float* src = img + i * npx;
+    float* src = img + i * npx;
     float* Ri = R + (size_t)i * ny * (nx + 4);
     float* Ti = T + (size_t)i * nx * (ny + 4);
+    const bool upd = MODE == 2 && active[i];
+    const float b = MODE == 2 ? (float)bcoef[i] : 0.f;
     for (int k = threadIdx.y; k < 32; k += 8) {
         const int x = x0 + threadIdx.x, y = y0 + k;
         float v = 0.f;
         if (x < nx && y < ny) {
-            v = src[(size_t)y * nx + x];
+            const size_t idx = (size_t)y * nx + x;
+            v = src[idx];
+            if (upd) {
+                v = fmaf(b, v, gr[i * npx + idx]);
+                src[idx] = v;
+            }
+            if (MODE == 1) cp[i * npx + idx] = v;
             Ri[(size_t)y * (nx + 4) + x + 2] = v;
         }
         tile[k][threadIdx.x] = v;
@@ -72,7 +87,24 @@ __global__ void __launch_bounds__(256) k_prep_dual(const float* __restrict__ img
 cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R, float* T,
                              cudaStream_t st) {
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32, g->N), blk(32, 8);
-    k_prep_dual<<<grid, blk, 0, st>>>(img, R, T, g->nx, g->ny);
+    k_prep_dual<0><<<grid, blk, 0, st>>>(const_cast<float*>(img), R, T, nullptr, nullptr, nullptr,
+                                         nullptr, g->nx, g->ny);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_dual_copy(const tnlm_geometry* g, const float* img, float* cp, float* R,
+                                  float* T, cudaStream_t st) {
+    dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32, g->N), blk(32, 8);
+    k_prep_dual<1><<<grid, blk, 0, st>>>(const_cast<float*>(img), R, T, cp, nullptr, nullptr,
+                                         nullptr, g->nx, g->ny);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_dual_update(const tnlm_geometry* g, float* s, const float* gr,
+                                    const double* bcoef, const int* active, float* R, float* T,
+                                    cudaStream_t st) {
+    dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32, g->N), blk(32, 8);
+    k_prep_dual<2><<<grid, blk, 0, st>>>(s, R, T, nullptr, gr, bcoef, active, g->nx, g->ny);
     return cudaGetLastError();
 }
 
