@@ -234,3 +234,23 @@ def test_batch_workload_sampled_slices_match_oracle(tn, oracle_mod):
         got = f.double().cpu().numpy()
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 1e-3, (c.name, err)
+
+
+def test_batch_edge_rules_zero_iterations_and_first_check(tn):
+    """Degenerate stopping rules in one batched launch: a slice with K = 0
+    is left untouched, a slice whose tolerance holds at its first check stops
+    after one iteration, the others run their K; each matches its single
+    call bitwise."""
+    cases = small_slices()
+    rules = [(0, 0.0, 1), (6, 1.0, 1), (4, 0.0, 1), (5, 0.0, 1)]
+    plist = tol_params(cases, rules)
+    geoms, ys, ws, fs, ref, ref_it = run_pair(tn, cases, plist)
+    assert ref_it == [0, 1, 4, 5]
+    f_before = [f.clone() for f in fs]
+    reps = tn.tnlm_reconstruct_batch(geoms, plist, ys, ws, fs, autotune=False)
+    torch.cuda.synchronize()
+    assert tn.tnlm_batch_last_was_loop()
+    assert [r["iterations"] for r in reps] == ref_it
+    assert torch.equal(fs[0], f_before[0])
+    for c, f, r in zip(cases, fs, ref):
+        assert torch.equal(f, r), c.name
