@@ -128,10 +128,10 @@ tnlm_status tnlm_project(const tnlm_geometry* geom, const float* d_img, float* d
  * has no counterpart in the paper.)  tnlm_project keeps its layout copies in
  * the handle's workspace, which is sized for a whole reconstruction and
  * allocated on first use; this variant allocates nothing: its scratch is a
- * file-scope device array of 6 Mi floats (24 MiB) that every GPU which loads
+ * file-scope device array of 12 Mi floats (48 MiB) that every GPU which loads
  * the library holds until the process exits.
- *   - Limit: N * (ny * (nx + 4) + nx * (ny + 4)) floats plus alignment must fit
- *     in 6 Mi floats (e.g. 10 phases of 512 x 512); larger geometries return
+ *   - Limit: 2 * N * (ny * (nx + 4) + nx * (ny + 4)) floats plus alignment must
+ *     fit in 12 Mi floats (e.g. 10 phases of 512 x 512); larger geometries return
  *     TNLM_ERR_INVALID_ARG and nothing is launched.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call

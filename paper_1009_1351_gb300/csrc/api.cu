@@ -148,7 +148,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 // Byte layout of the workspace for window radius rho and history capacity kcap.
 struct WsLayout {
-    size_t off_u, off_s, off_gr, off_R, off_T, off_r, off_z, off_t, off_sw, off_bps, off_D, off_U0, off_U1,
+    size_t off_u, off_s, off_s2, off_gr, off_R, off_T, off_r, off_z, off_t, off_sw, off_bps, off_D, off_U0, off_U1,
         off_mins, off_zn, off_part, off_part2, off_gjs, off_gjc, off_state, total;
     size_t part_len, part2_len;
     PadPlane pp;
@@ -172,9 +172,10 @@ WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
     auto take = [&](size_t bytes) { size_t r = o; o = align_up(o + bytes, 256); return r; };
     L.off_u = take(4 * npx * N);
     L.off_s = take(4 * npx * N);
+    L.off_s2 = take(4 * npx * N);
     L.off_gr = take(4 * npx * N);
-    L.off_R = take(4 * (size_t)g->ny * (g->nx + 4) * N);
-    L.off_T = take(4 * (size_t)g->nx * (g->ny + 4) * N);
+    L.off_R = take(8 * (size_t)g->ny * (g->nx + 4) * N);    // float2 pairs
+    L.off_T = take(8 * (size_t)g->nx * (g->ny + 4) * N);
     L.off_r = take(4 * nsg * N);
     L.off_z = take(4 * nsg * N);
     L.off_t = take(4 * nsg * N);
@@ -222,6 +223,7 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     ws.kcap = nk < 1 ? 1 : nk;
     ws.u = (float*)(b + L.off_u);
     ws.s = (float*)(b + L.off_s);
+    ws.s2 = (float*)(b + L.off_s2);
     ws.gr = (float*)(b + L.off_gr);
     ws.R = (float*)(b + L.off_R);
     ws.T = (float*)(b + L.off_T);
@@ -282,21 +284,27 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     if (p->data_step == TNLM_DATA_GRAD) {
         LK(TNLM_KCLASS_CGLS, launch_grad_final(g, ws, p->beta, st), "gradient step");
     } else {
+        // the direction lives in sbuf[cur]; each update writes the other buffer
+        float* sbuf[2] = {ws.s, ws.s2};
+        int cur = 0;
         for (int m = 0; m < p->m1; ++m) {
             const bool last = m == p->m1 - 1;
             // from the second step on, the direction update s = P_n^T r + b s
             // is fused into the layout preparation of s
-            if (m == 0)
-                LK(TNLM_KCLASS_PREP, launch_prep_dual(g, ws.s, ws.R, ws.T, st), "prep");
-            else
+            if (m == 0) {
+                LK(TNLM_KCLASS_PREP, launch_prep_dual(g, sbuf[0], ws.R, ws.T, st), "prep");
+            } else {
                 LK(TNLM_KCLASS_PREP,
-                   launch_prep_dual_update(g, ws.s, ws.gr, ws.st.b, ws.st.active, ws.R, ws.T, st),
+                   launch_prep_dual_update(g, sbuf[cur], sbuf[cur ^ 1], ws.gr, ws.st.b, ws.st.active,
+                                           ws.R, ws.T, st),
                    "cgls s + prep");
+                cur ^= 1;
+            }
             ProjOut ot{};
             ot.mode = 2; ot.q = ws.t; ot.sw = ws.sw; ot.part = part_s;
             LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, ot, st), "project");
             LK(TNLM_KCLASS_CGLS, launch_cgls_a(g, ws, st), "cgls a");
-            LK(TNLM_KCLASS_CGLS, launch_cgls_update_ur(g, ws, !last, st), "cgls update");
+            LK(TNLM_KCLASS_CGLS, launch_cgls_update_ur(g, ws, sbuf[cur], !last, st), "cgls update");
             if (last) break;
             LK(TNLM_KCLASS_BACKPROJECT, launch_backproject(g, ws.z, ws.gr, part_i, ws.bps, st), "backproject");
             LK(TNLM_KCLASS_CGLS, launch_cgls_b(g, ws, st), "cgls b");
@@ -869,6 +877,7 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
     // per-view (cos t, sin t), per-bin (cos g, sin g), per-ray chord constants (FP64 -> FP32)
     std::vector<float2> hv(NV), hb(g->B);
     std::vector<float4> hr(NV * g->B);
+    std::vector<int4> hc(NV);
     const double dg_ = g->bin_mm / g->sdd;
     for (int b = 0; b < g->B; ++b) {
         const double ga = (b - 0.5 * (g->B - 1)) * dg_;
@@ -883,6 +892,11 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
     for (size_t v = 0; v < NV; ++v) {
         const double t = d->view_angles_rad[v];
         hv[v] = make_float2((float)cos(t), (float)sin(t));
+        // the ray direction turns monotonically with b, so the rays of one
+        // class normally form one bin run (at most one class change within a
+        // fan narrower than 90 degrees); otherwise both ranges are the whole
+        // detector and the backprojector tests every ray's class
+        int first_cls = 0, prev_cls = 0, changes = 0, split = g->B;
         for (int b = 0; b < g->B; ++b) {
             const double ga = (b - 0.5 * (g->B - 1)) * dg_;
             const double ux = -cos(t + ga), uy = -sin(t + ga);
@@ -900,7 +914,15 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
                 L = -g->pixel / fabs(uy);
             }
             hr[v * g->B + b] = make_float4((float)kk, (float)alpha, (float)ik, (float)L);
+            const int cls = L > 0.0 ? 0 : 1;
+            if (b == 0) first_cls = cls;
+            else if (cls != prev_cls && changes++ == 0) split = b;
+            prev_cls = cls;
         }
+        const int last = g->B - 1;
+        if (changes > 1) hc[v] = make_int4(0, last, 0, last);
+        else if (first_cls == 0) hc[v] = make_int4(0, split - 1, split, last);
+        else hc[v] = make_int4(split, last, 0, split - 1);
     }
     // taps of the discrete equiangular ramp kernel (initial FBP)
     std::vector<float> ht(2 * (size_t)g->B - 1);
@@ -913,24 +935,27 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
         }
         ht[n + g->B - 1] = (float)v;
     }
-    void *pv = nullptr, *pb = nullptr, *pr = nullptr, *pt = nullptr;
+    void *pv = nullptr, *pb = nullptr, *pr = nullptr, *pt = nullptr, *pc = nullptr;
     cudaError_t e = dev_alloc(&pv, sizeof(float2) * NV);
     if (e == cudaSuccess) e = dev_alloc(&pb, sizeof(float2) * g->B);
     if (e == cudaSuccess) e = dev_alloc(&pr, sizeof(float4) * NV * g->B);
     if (e == cudaSuccess) e = dev_alloc(&pt, sizeof(float) * ht.size());
+    if (e == cudaSuccess) e = dev_alloc(&pc, sizeof(int4) * NV);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFree(pv); cudaFree(pb); cudaFree(pr); cudaFree(pt);
+        cudaFree(pv); cudaFree(pb); cudaFree(pr); cudaFree(pt); cudaFree(pc);
         delete g;
         return fail(e == cudaErrorMemoryAllocation ? TNLM_ERR_OOM : TNLM_ERR_CUDA,
                     "geometry table allocation failed: %s", cudaGetErrorString(e));
     }
     g->d_view = (float2*)pv; g->d_bin = (float2*)pb; g->d_ray = (float4*)pr;
     g->d_fbp_taps = (float*)pt;
+    g->d_vcls = (int4*)pc;
     e = cudaMemcpy(pv, hv.data(), sizeof(float2) * NV, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pb, hb.data(), sizeof(float2) * g->B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pr, hr.data(), sizeof(float4) * NV * g->B, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(pt, ht.data(), sizeof(float) * ht.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pc, hc.data(), sizeof(int4) * NV, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         tnlm_destroy_geometry(g);
         return cuda_fail(e, "geometry table upload");
@@ -955,6 +980,7 @@ void tnlm_destroy_geometry(tnlm_geometry* g) {
     cudaFree(g->d_bin);
     cudaFree(g->d_ray);
     cudaFree(g->d_fbp_taps);
+    cudaFree(g->d_vcls);
     cudaFree(g->ws.base);
     if (g->graph) {
         GraphState* G = (GraphState*)g->graph;
@@ -1029,9 +1055,10 @@ tnlm_status tnlm_project_static(const tnlm_geometry* gc, const float* d_img, flo
     if (!d_img || !d_sino) return fail(TNLM_ERR_INVALID_ARG, "NULL buffer");
     if (!aligned16(d_img) || !aligned16(d_sino)) return fail(TNLM_ERR_INVALID_ARG, "buffers must be 16-byte aligned");
     tnlm_geometry* g = const_cast<tnlm_geometry*>(gc);
-    // row-major and column-major padded copies of the image, back to back
-    const size_t nR = align_up((size_t)g->N * g->ny * (g->nx + 4), 64);
-    const size_t nT = (size_t)g->N * g->nx * (g->ny + 4);
+    // row-major and column-major padded copies of the image (float2 pairs),
+    // back to back
+    const size_t nR = align_up(2 * (size_t)g->N * g->ny * (g->nx + 4), 64);
+    const size_t nT = 2 * (size_t)g->N * g->nx * (g->ny + 4);
     if (nR + nT > static_scratch_floats())
         return fail(TNLM_ERR_INVALID_ARG,
                     "image too large for the static scratch: needs %zu floats, the array holds %zu",

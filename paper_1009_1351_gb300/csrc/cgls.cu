@@ -141,11 +141,11 @@ static int grid_for(size_t n) {
     return (int)b;
 }
 
-cudaError_t launch_cgls_update_ur(const tnlm_geometry* g, const Workspace& ws, bool with_r,
-                                  cudaStream_t st) {
+cudaError_t launch_cgls_update_ur(const tnlm_geometry* g, const Workspace& ws, const float* s,
+                                  bool with_r, cudaStream_t st) {
     const size_t npx = (size_t)g->nx * g->ny, nsg = (size_t)g->V * g->B;
     const size_t n = npx * g->N + (with_r ? nsg * g->N : 0);
-    k_cgls_update_ur<<<grid_for(n), 256, 0, st>>>(ws.u, ws.s, ws.r, ws.z, ws.t, ws.sw, ws.st.a,
+    k_cgls_update_ur<<<grid_for(n), 256, 0, st>>>(ws.u, s, ws.r, ws.z, ws.t, ws.sw, ws.st.a,
                                                    npx, nsg, g->N, with_r ? 1 : 0);
     return cudaGetLastError();
 }

@@ -3,10 +3,12 @@
 // Data layout in HBM (per geometry handle; N phases, image nx x ny, V views,
 // B bins, window W = 2*rho+1):
 //   images        [N][ny][nx]             f, u (CGLS iterate / g), s, grad
-//   dual layout   R [N][ny][nx+4], T [N][nx][ny+4]: the projector's input in
-//                 row-major and column-major form with two zero pad lines on
-//                 each side, so that every ray reads consecutive addresses
-//                 across a warp whichever axis it marches along.
+//   dual layout   R [N][ny][nx+4], T [N][nx][ny+4] of float2: the projector's
+//                 input in row-major and column-major form with two zero pad
+//                 positions on each side of a line, entry q holding
+//                 (X[q] - X[q+1], X[q+1]), so that every ray reads one pair
+//                 per line at consecutive addresses across a warp whichever
+//                 axis it marches along.
 //   sinograms     [N][V][B]               r, z = sqrt(w) r, t, sqrt(w)
 //   D planes      [N pairs][W*W][py][px]  patch distances of pair (i, i+1)
 //                 with a halo of rho rows and ox >= rho columns holding +inf
@@ -56,7 +58,8 @@ struct Workspace {
     int kcap = 0;      // history capacity
     // images
     float *u = nullptr, *s = nullptr, *gr = nullptr;
-    float *R = nullptr, *T = nullptr;
+    float* s2 = nullptr;     // CGLS direction, second buffer (updates alternate between s and s2)
+    float *R = nullptr, *T = nullptr;   // float2 pairs (see the dual layout above)
     // sinograms
     float *r = nullptr, *z = nullptr, *t = nullptr, *sw = nullptr;
     float* bps = nullptr;    // backprojection partial images [4][N][ny][nx]
@@ -93,6 +96,8 @@ struct tnlm_geometry {
     float2* d_view = nullptr;   // [N*V] (cos t, sin t)
     float2* d_bin = nullptr;    // [B] (cos g, sin g)
     float4* d_ray = nullptr;    // [N*V*B] per-ray marching constants (kk, alpha, 1/|kk|, +-L)
+    int4* d_vcls = nullptr;     // [N*V] bin ranges (lo, hi) of the column-marching rays (x, y)
+                                // and of the row-marching rays (z, w) of each view; lo > hi: none
     float* d_fbp_taps = nullptr; // [2B-1] discrete equiangular ramp kernel of the initial FBP
     tnlm::Workspace ws;
     int cta_slots_bp = 0;       // resident backprojector CTAs on the device
@@ -130,7 +135,7 @@ cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R,
                              cudaStream_t st);
 cudaError_t launch_prep_dual_copy(const tnlm_geometry* g, const float* img, float* cp, float* R,
                                   float* T, cudaStream_t st);
-cudaError_t launch_prep_dual_update(const tnlm_geometry* g, float* s, const float* gr,
+cudaError_t launch_prep_dual_update(const tnlm_geometry* g, const float* s, float* s_new, const float* gr,
                                     const double* bcoef, const int* active, float* R, float* T,
                                     cudaStream_t st);
 cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
@@ -160,7 +165,7 @@ cudaError_t launch_fbp_phases(const tnlm_geometry* g, const float* y, float* Q, 
 cudaError_t launch_cgls_init_scalars(const tnlm_geometry* g, const Workspace& ws,
                                      cudaStream_t st);
 cudaError_t launch_cgls_a(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st);
-cudaError_t launch_cgls_update_ur(const tnlm_geometry* g, const Workspace& ws, bool with_r,
+cudaError_t launch_cgls_update_ur(const tnlm_geometry* g, const Workspace& ws, const float* s, bool with_r,
                                   cudaStream_t st);
 cudaError_t launch_cgls_b(const tnlm_geometry* g, const Workspace& ws, cudaStream_t st);
 cudaError_t launch_grad_final(const tnlm_geometry* g, const Workspace& ws, double beta,

@@ -14,16 +14,21 @@
 // of a warp walk the union of their column ranges in lock step.
 //
 // K2 (k_backproject): the transpose as an atomic-free gather.  A block owns
-// a 32 x 32 pixel tile of one phase; its 8 warps take every 8th view.  For a
-// view, the rays that can touch the tile form one bin range (from the fan
-// angles of the tile corners).  All 32 lanes of a warp handle the same ray at
-// once: for a column-marching ray lane c is tile column c and, with the very
-// same floating-point steps as K1, finds the ray's rows lo, lo+1 in that
-// column and adds frac * L * z and (1 - frac) * L * z to the warp's private
-// accumulator tile; a row-marching ray is handled the same way with lane c as
-// tile row c.  The private tiles are summed in a fixed order at the end, so
-// the result is bitwise reproducible, and every matrix entry is formed by the
-// same FP32 operations on the same per-ray constants as in K1.
+// a 32 x 32 pixel tile of one phase.  Four of its 8 warps deposit the
+// column-marching rays and four the row-marching rays; the four warps of a
+// class take every 4th view.  For a view, the rays that can touch the tile
+// form one bin range (from the fan angles of the tile corners), cut to the
+// bins of the warp's class (one run per view, tabulated at geometry
+// creation).  All 32 lanes of a warp handle the same ray at once: for a
+// column-marching ray lane c is tile column c and, with the very same
+// floating-point steps as K1, finds the ray's rows lo, lo+1 in that column
+// and adds frac * L * z and (1 - frac) * L * z to the warp's private
+// accumulator tile; a row-marching ray is handled the same way with lane c
+// as tile row c.  One class per warp means one private tile per warp, which
+// keeps five blocks resident per SM.  The private tiles are summed in a
+// fixed order at the end, so the result is bitwise reproducible, and every
+// matrix entry is formed by the same FP32 operations on the same per-ray
+// constants as in K1.
 //
 // Per-ray constants (built in FP64 on the host at geometry creation):
 //   float4 (kk, alpha, ik, L): the position across the marching lines at the
@@ -39,72 +44,91 @@
 namespace tnlm {
 
 // ---------------------------------------------------------------------------
-// Dual layout: R[i][iy][ix+2] (row-major, two zero columns each side) and
-// T[i][ix][iy+2] (column-major, two zero rows each side).  Pads are zeroed
-// once when the workspace is created and never written.
+// Dual layout of pairs.  Along each line of the row-major copy R [N][ny][nx+4]
+// and of the column-major copy T [N][nx][ny+4] (two pad positions on each
+// side of the nx or ny interior ones, X[q] = 0 there), entry q holds the
+// float2 (X[q] - X[q+1], X[q+1]): the two values a ray meets in a line, with
+// the difference the projector's interpolation takes, so K1 reads one 8-byte
+// pair per line and forms exactly the FP32 values it would form from X[q] and
+// X[q+1].  Entries 1 .. n+1 depend on the image and are written here; the
+// others stay zero from the workspace clear.
 // ---------------------------------------------------------------------------
 // MODE 0: R, T of img.  MODE 1: also a copy of img into cp (u^(0) = f).
-// MODE 2: first the CGLS direction update img = gr + b_i img (for phases
-// whose CGLS is still active; the same FP32 operation as a separate update
-// kernel would do), written back, then R, T of the result.
+// MODE 2: first the CGLS direction update cp = gr + b_i img (for phases
+// whose CGLS is still active, else cp = img; the same FP32 operation as a
+// separate update kernel would do), then R, T of the result.  img is never
+// written: a block also updates the pixels of the row and column beyond its
+// tile for their pairs, from the values of img before the update.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_prep_dual(float* __restrict__ img, float* __restrict__ R,
-                                                   float* __restrict__ T, float* __restrict__ cp,
+__global__ void __launch_bounds__(256) k_prep_dual(const float* __restrict__ img, float2* __restrict__ R,
+                                                   float2* __restrict__ T, float* __restrict__ cp,
                                                    const float* __restrict__ gr,
                                                    const double* __restrict__ bcoef,
                                                    const int* __restrict__ active, int nx, int ny) {
-    __shared__ float tile[32][33];
+    __shared__ float tile[33][33];   // [row][col]: the 32 x 32 tile and one more row and column
     const int i = blockIdx.z;
     const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
     const size_t npx = (size_t)nx * ny;
-    float* src = img + i * npx;
-    float* Ri = R + (size_t)i * ny * (nx + 4);
-    float* Ti = T + (size_t)i * nx * (ny + 4);
+    const float* src = img + i * npx;
+    float2* Ri = R + (size_t)i * ny * (nx + 4);
+    float2* Ti = T + (size_t)i * nx * (ny + 4);
     const bool upd = MODE == 2 && active[i];
     const float b = MODE == 2 ? (float)bcoef[i] : 0.f;
-    for (int k = threadIdx.y; k < 32; k += 8) {
-        const int x = x0 + threadIdx.x, y = y0 + k;
+    for (int e = tid; e < 33 * 33; e += 256) {
+        const int k = e / 33, c = e - k * 33;
+        const int x = x0 + c, y = y0 + k;
         float v = 0.f;
         if (x < nx && y < ny) {
             const size_t idx = (size_t)y * nx + x;
             v = src[idx];
-            if (upd) {
-                v = fmaf(b, v, gr[i * npx + idx]);
-                src[idx] = v;
-            }
-            if (MODE == 1) cp[i * npx + idx] = v;
-            Ri[(size_t)y * (nx + 4) + x + 2] = v;
+            if (upd) v = fmaf(b, v, gr[i * npx + idx]);
+            if (MODE != 0 && k < 32 && c < 32) cp[i * npx + idx] = v;   // this block's own pixels
         }
-        tile[k][threadIdx.x] = v;
+        tile[k][c] = v;
     }
     __syncthreads();
+    const int tx = threadIdx.x;
     for (int k = threadIdx.y; k < 32; k += 8) {
-        const int y = y0 + threadIdx.x, x = x0 + k;
-        if (x < nx && y < ny) Ti[(size_t)x * (ny + 4) + y + 2] = tile[threadIdx.x][k];
+        const int x = x0 + tx, y = y0 + k;        // row pairs, lanes along the row
+        if (x < nx && y < ny) {
+            float2* line = Ri + (size_t)y * (nx + 4);
+            const float v0 = tile[k][tx], v1 = tile[k][tx + 1];
+            line[x + 2] = make_float2(v0 - v1, v1);
+            if (x == 0) line[1] = make_float2(0.f - v0, v0);
+        }
+        const int xc = x0 + k, yc = y0 + tx;      // column pairs, lanes along the column
+        if (xc < nx && yc < ny) {
+            float2* line = Ti + (size_t)xc * (ny + 4);
+            const float v0 = tile[tx][k], v1 = tile[tx + 1][k];
+            line[yc + 2] = make_float2(v0 - v1, v1);
+            if (yc == 0) line[1] = make_float2(0.f - v0, v0);
+        }
     }
 }
 
 cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R, float* T,
                              cudaStream_t st) {
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32, g->N), blk(32, 8);
-    k_prep_dual<0><<<grid, blk, 0, st>>>(const_cast<float*>(img), R, T, nullptr, nullptr, nullptr,
-                                         nullptr, g->nx, g->ny);
+    k_prep_dual<0><<<grid, blk, 0, st>>>(img, (float2*)R, (float2*)T, nullptr,
+                                         nullptr, nullptr, nullptr, g->nx, g->ny);
     return cudaGetLastError();
 }
 
 cudaError_t launch_prep_dual_copy(const tnlm_geometry* g, const float* img, float* cp, float* R,
                                   float* T, cudaStream_t st) {
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32, g->N), blk(32, 8);
-    k_prep_dual<1><<<grid, blk, 0, st>>>(const_cast<float*>(img), R, T, cp, nullptr, nullptr,
-                                         nullptr, g->nx, g->ny);
+    k_prep_dual<1><<<grid, blk, 0, st>>>(img, (float2*)R, (float2*)T, cp,
+                                         nullptr, nullptr, nullptr, g->nx, g->ny);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_dual_update(const tnlm_geometry* g, float* s, const float* gr,
-                                    const double* bcoef, const int* active, float* R, float* T,
-                                    cudaStream_t st) {
+cudaError_t launch_prep_dual_update(const tnlm_geometry* g, const float* s, float* s_new,
+                                    const float* gr, const double* bcoef, const int* active,
+                                    float* R, float* T, cudaStream_t st) {
     dim3 grid((g->nx + 31) / 32, (g->ny + 31) / 32, g->N), blk(32, 8);
-    k_prep_dual<2><<<grid, blk, 0, st>>>(s, R, T, nullptr, gr, bcoef, active, g->nx, g->ny);
+    k_prep_dual<2><<<grid, blk, 0, st>>>(s, (float2*)R, (float2*)T, s_new, gr, bcoef, active,
+                                         g->nx, g->ny);
     return cudaGetLastError();
 }
 
@@ -112,8 +136,8 @@ cudaError_t launch_prep_dual_update(const tnlm_geometry* g, float* s, const floa
 // K1
 // ---------------------------------------------------------------------------
 struct ProjArgs {
-    const float* R;
-    const float* T;
+    const float2* R;
+    const float2* T;
     const float4* ray;
     int nx, ny, V, B, nchunk;
     ProjOut o;
@@ -138,11 +162,13 @@ __device__ __forceinline__ Cut line_cut(float kk, float am, float ik, float kf, 
 }
 
 // March one ray over 'lines' (columns of T or rows of R) lo..hi.  base points
-// at the first interior element of line 0 of the phase; 'pitch' is the line
-// stride; 'nacross' the interior length of a line.  The position across the
-// line at the start of line k is alpha + kk*k (pixel units); am = alpha +
-// min(kk, 0) is the lower end of the ray's span inside line 0.
-__device__ __forceinline__ float march(const float* __restrict__ base, int pitch, int nacross,
+// at the pair of the first interior element of line 0 of the phase; 'pitch'
+// is the line stride in pairs; 'nacross' the interior length of a line.  The
+// position across the line at the start of line k is alpha + kk*k (pixel
+// units); am = alpha + min(kk, 0) is the lower end of the ray's span inside
+// line 0.  With v0, v1 the values at the lower line index and the next, the
+// pair holds (v0 - v1, v1) and the ray accumulates frac * (v0 - v1) + v1.
+__device__ __forceinline__ float march(const float2* __restrict__ base, int pitch, int nacross,
                                        float kk, float am, float ik, int lo, int hi, bool on) {
     float acc = 0.f;
     float kf = (float)lo;
@@ -152,9 +178,8 @@ __device__ __forceinline__ float march(const float* __restrict__ base, int pitch
     for (int k = lo; k <= hi; ++k) {
         const Cut c = line_cut(kk, am, ik, kf, na);
         if (on) {
-            const float* p = base + (koff + c.j);
-            const float v0 = __ldg(p), v1 = __ldg(p + 1);
-            acc = fmaf(c.frac, v0 - v1, acc + v1);
+            const float2 pv = __ldg(base + (koff + c.j));
+            acc = fmaf(c.frac, pv.x, acc + pv.y);
         }
         kf += 1.f;
         koff += pitch;
@@ -204,8 +229,8 @@ __global__ void __launch_bounds__(kProjThreads) k_project(ProjArgs a) {
         if (__ballot_sync(full, any)) {
             const int wl = __reduce_min_sync(full, any ? lo : 0x7fffffff);
             const int wh = __reduce_max_sync(full, any ? hi : -1);
-            const float* base = cls == 0 ? a.T + (size_t)phase * a.nx * (a.ny + 4) + 2
-                                         : a.R + (size_t)phase * a.ny * (a.nx + 4) + 2;
+            const float2* base = cls == 0 ? a.T + (size_t)phase * a.nx * (a.ny + 4) + 2
+                                          : a.R + (size_t)phase * a.ny * (a.nx + 4) + 2;
             const float acc = march(base, nacross + 4, nacross, rp.x, rp.y + fminf(rp.x, 0.f), rp.z,
                                     wl, wh, in);
             if (in) q = acc * fabsf(rp.w);
@@ -243,7 +268,7 @@ int proj_chunks(const tnlm_geometry* g) { return (g->B + kProjThreads - 1) / kPr
 cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* T,
                            const ProjOut& o, cudaStream_t st) {
     ProjArgs a;
-    a.R = R; a.T = T; a.ray = g->d_ray;
+    a.R = (const float2*)R; a.T = (const float2*)T; a.ray = g->d_ray;
     a.nx = g->nx; a.ny = g->ny; a.V = g->V; a.B = g->B; a.nchunk = proj_chunks(g);
     a.o = o;
     dim3 grid(a.nchunk * g->N * g->V);
@@ -259,7 +284,8 @@ cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* 
 // K2
 // ---------------------------------------------------------------------------
 constexpr int kBpT = 32;        // tile side
-constexpr int kBpWarps = 8;
+constexpr int kBpWarps = 8;     // per block: kBpClassWarps per ray class
+constexpr int kBpClassWarps = kBpWarps / 2;
 constexpr int kBpMaxGroups = 4;  // view groups per tile (CTAs per tile)
 
 struct BpArgs {
@@ -269,12 +295,13 @@ struct BpArgs {
     double* part;          // nullable: per-tile partial sums of img^2
     const float2* view;
     const float4* ray;
+    const int4* vcls;      // per view: bin ranges of the two ray classes
     int nx, ny, V, B, G;
     float sidp, inv_dg, half_b;
 };
 
 size_t bp_smem_bytes() {
-    return sizeof(float) * (2 * kBpWarps * kBpT * kBpT + kBpT * (kBpT + 1)) +
+    return sizeof(float) * (kBpWarps * kBpT * kBpT + kBpT * (kBpT + 1)) +
            sizeof(float4) * kBpWarps * 32;
 }
 
@@ -294,37 +321,47 @@ __device__ __forceinline__ void deposit(float* acc, float kk, float am, float ik
     if ((unsigned)(r0 + 1) < n) acc[(r0 + 1) * 32] += fmaf(-frac, Lz, Lz);
 }
 
+// The first kBpClassWarps warps deposit the column-marching rays (lane =
+// tile column, private tile [row][col]), the others the row-marching rays
+// (lane = tile row, private tile [col][row]); both layouts are conflict-free
+// for their class, and each warp needs only one private tile.
 // DIRECT: the block sees all views of its tile and writes the image (and the
 // squared-norm partial); otherwise it writes its view group's partial image.
 template <bool DIRECT, bool PART>
-__global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
+__global__ void __launch_bounds__(kBpWarps * 32, 5) k_backproject(BpArgs a) {
     extern __shared__ float sm[];
-    float* accC = sm;                                   // [warp][row][col]
-    float* accR = accC + kBpWarps * kBpT * kBpT;        // [warp][col][row]
-    float* tsum = accR + kBpWarps * kBpT * kBpT;        // [row][col + 1]
+    float* acc = sm;                                    // [warp][32][32]
+    float* tsum = acc + kBpWarps * kBpT * kBpT;         // [row][col + 1]
     float4* stg = (float4*)(tsum + kBpT * (kBpT + 1));  // [warp][32]
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const bool colw = w < kBpClassWarps;                // warp-uniform
     const int X0 = blockIdx.x * kBpT, Y0 = blockIdx.y * kBpT;
     const int phase = blockIdx.z / a.G, grp = blockIdx.z - phase * a.G;
     const int ncols = min(kBpT, a.nx - X0), nrows = min(kBpT, a.ny - Y0);
-    for (int k = tid; k < 2 * kBpWarps * kBpT * kBpT; k += blockDim.x) sm[k] = 0.f;
+    for (int k = tid; k < kBpWarps * kBpT * kBpT; k += blockDim.x) sm[k] = 0.f;
     __syncthreads();
-    float* myC = accC + w * kBpT * kBpT + lane;
-    float* myR = accR + w * kBpT * kBpT + lane;
+    float* my = acc + w * kBpT * kBpT + lane;
     float4* myS = stg + w * 32;
+    // this lane's marching line (tile column or row), the origin and count of
+    // the lines across it, and whether the lane's line lies in the image
+    const float kf = colw ? (float)(X0 + lane) : (float)(Y0 + lane);
+    const int j0 = colw ? Y0 : X0;
+    const unsigned nacross = (unsigned)(colw ? nrows : ncols);
+    const int nalong = colw ? ncols : nrows;
+    const bool lane_on = lane < nalong;
     // tile corners (pixel units about the isocentre), clipped to the image
     const float xa = X0 - 0.5f * a.nx, xb = X0 + ncols - 0.5f * a.nx;
     const float ya = Y0 - 0.5f * a.ny, yb = Y0 + nrows - 0.5f * a.ny;
     const unsigned full = 0xffffffffu;
-    const float kfc = (float)(X0 + lane), kfr = (float)(Y0 + lane);  // this lane's column / row
-    const int S = kBpWarps * a.G;              // view stride of a warp
-    const int gw = grp * kBpWarps + w;         // first view of this warp
+    const int S = kBpClassWarps * a.G;                      // view stride of a warp
+    const int gw = grp * kBpClassWarps + (w % kBpClassWarps);  // first view of this warp
     const float4* rays = a.ray + (size_t)phase * a.V * a.B;
     const float* zs = a.sino + (size_t)phase * a.V * a.B;
     const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
 
     for (int m0 = 0; gw + S * m0 < a.V; m0 += 32) {
-        // bin ranges of the next 32 views of this warp, one view per lane
+        // bin ranges of this warp's class in the next 32 views of this warp,
+        // one view per lane
         const int vl = gw + S * (m0 + lane);
         int lo = 1, hi = 0;
         if (vl < a.V) {
@@ -339,8 +376,9 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
                 bmin = fminf(bmin, bc);
                 bmax = fmaxf(bmax, bc);
             }
-            lo = max(0, (int)floorf(bmin) - 1);
-            hi = min(a.B - 1, (int)ceilf(bmax) + 1);
+            const int4 cr = a.vcls[(size_t)phase * a.V + vl];
+            lo = max(max(0, (int)floorf(bmin) - 1), colw ? cr.x : cr.z);
+            hi = min(min(a.B - 1, (int)ceilf(bmax) + 1), colw ? cr.y : cr.w);
         }
         const unsigned todo = __ballot_sync(full, lo <= hi);
         if (!todo) continue;
@@ -374,35 +412,26 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
                     nzz = __ldg(zs + nrb + lane);
                 }
             }
-            // bit t: staged ray t marches over columns (L > 0)
-            const unsigned colmask = __ballot_sync(full, lane < nb && rp.w > 0.f);
+            // bit t: staged ray t is of this warp's class
+            const unsigned mine =
+                __ballot_sync(full, lane < nb && (colw ? rp.w > 0.f : !(rp.w > 0.f)));
             __syncwarp();
             myS[lane] = make_float4(rp.x, rp.y + fminf(rp.x, 0.f), rp.z, fabsf(rp.w) * zz);
             __syncwarp();
             const unsigned staged = nb >= 32 ? full : (1u << nb) - 1u;
-            if (colmask == staged && ncols == kBpT) {
-                // the usual case: one class for the whole chunk, a full tile
-                // side of lanes -- no per-ray class or lane test
+            if (mine == staged && nalong == kBpT) {
+                // the usual case: every staged ray is of this class and the
+                // tile side is full -- no per-ray class or lane test
 #pragma unroll 4
                 for (int t = 0; t < nb; ++t) {
                     const float4 r = myS[t];
-                    deposit(myC, r.x, r.y, r.z, r.w, kfc, Y0, (unsigned)nrows);
-                }
-            } else if (colmask == 0u && nrows == kBpT) {
-#pragma unroll 4
-                for (int t = 0; t < nb; ++t) {
-                    const float4 r = myS[t];
-                    deposit(myR, r.x, r.y, r.z, r.w, kfr, X0, (unsigned)ncols);
+                    deposit(my, r.x, r.y, r.z, r.w, kf, j0, nacross);
                 }
             } else {
 #pragma unroll 2
                 for (int t = 0; t < nb; ++t) {
                     const float4 r = myS[t];
-                    if ((colmask >> t) & 1u) {
-                        if (lane < ncols) deposit(myC, r.x, r.y, r.z, r.w, kfc, Y0, (unsigned)nrows);
-                    } else {
-                        if (lane < nrows) deposit(myR, r.x, r.y, r.z, r.w, kfr, X0, (unsigned)ncols);
-                    }
+                    if (((mine >> t) & 1u) && lane_on) deposit(my, r.x, r.y, r.z, r.w, kf, j0, nacross);
                 }
             }
             if (nvi < 0) break;
@@ -415,7 +444,7 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
         const int r = k >> 5, c = k & 31;
         float s = 0.f;
 #pragma unroll
-        for (int ww = 0; ww < kBpWarps; ++ww) s += accC[(ww * kBpT + r) * kBpT + c];
+        for (int ww = 0; ww < kBpClassWarps; ++ww) s += acc[(ww * kBpT + r) * kBpT + c];
         tsum[r * (kBpT + 1) + c] = s;
     }
     __syncthreads();
@@ -423,7 +452,7 @@ __global__ void __launch_bounds__(kBpWarps * 32) k_backproject(BpArgs a) {
         const int c = k >> 5, r = k & 31;
         float s = tsum[r * (kBpT + 1) + c];
 #pragma unroll
-        for (int ww = 0; ww < kBpWarps; ++ww) s += accR[(ww * kBpT + c) * kBpT + r];
+        for (int ww = kBpClassWarps; ww < kBpWarps; ++ww) s += acc[(ww * kBpT + c) * kBpT + r];
         tsum[r * (kBpT + 1) + c] = s;
     }
     __syncthreads();
@@ -476,9 +505,6 @@ int bp_blocks_per_phase(const tnlm_geometry* g) {
     return ((g->nx + kBpT - 1) / kBpT) * ((g->ny + kBpT - 1) / kBpT);
 }
 
-// View groups per tile (CTAs per tile): the smallest G whose grid fills its
-// last wave to >= 85 % (else the best fill), from the occupancy of the
-// kernel and the device's SM count.  Each warp keeps at least one view.
 // Opt the backprojector variants into their dynamic shared memory and
 // count the CTA slots of the current device (called at geometry creation,
 // outside any stream capture).
@@ -499,24 +525,25 @@ cudaError_t prepare_backproject(int* slots) {
 }
 
 int bp_max_groups(const tnlm_geometry* g) {
-    const int m = (g->V + kBpWarps - 1) / kBpWarps;
+    const int m = (g->V + kBpClassWarps - 1) / kBpClassWarps;
     return m < kBpMaxGroups ? m : kBpMaxGroups;
 }
 
+// View groups per tile (CTAs per tile).  Tiles differ in cost (rays per
+// tile fall off towards the edge of the field of view), so the grid should
+// span about three waves of resident CTAs for the block scheduler to even
+// out: the smallest G that reaches three waves, else the largest G that
+// still leaves each warp at least 4 views (measured on 256^2 slices: with
+// 360 views one group per tile took 0.69 ms per call, four groups 0.55 ms).
 static int bp_groups(const tnlm_geometry* g) {
     if (g->tune_bp_groups > 0) return min(g->tune_bp_groups, bp_max_groups(g));
-    const int slots = g->cta_slots_bp > 0 ? g->cta_slots_bp : 1;
-    const int tiles = bp_blocks_per_phase(g) * g->N;
-    int best = 1;
-    double best_fill = 0.0;
-    for (int G = 1; G <= kBpMaxGroups && G <= (g->V + kBpWarps - 1) / kBpWarps; ++G) {
-        const long long ctas = (long long)tiles * G;
-        const long long waves = (ctas + slots - 1) / slots;
-        const double fill = (double)ctas / (double)(waves * slots);
-        if (fill >= 0.85) return G;
-        if (fill > best_fill + 1e-9) { best_fill = fill; best = G; }
-    }
-    return best;
+    const long long slots = g->cta_slots_bp > 0 ? g->cta_slots_bp : 1;
+    const long long tiles = (long long)bp_blocks_per_phase(g) * g->N;
+    int G = 1;
+    while (G < bp_max_groups(g) && tiles * G < 3 * slots &&
+           g->V >= 4 * kBpClassWarps * (G + 1))
+        ++G;
+    return G;
 }
 
 size_t bp_scratch_floats(const tnlm_geometry* g) {
@@ -533,7 +560,7 @@ cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float*
                                double* part, float* scratch, cudaStream_t st) {
     BpArgs a;
     a.sino = sino; a.img = img; a.part = part; a.scratch = scratch;
-    a.view = g->d_view; a.ray = g->d_ray;
+    a.view = g->d_view; a.ray = g->d_ray; a.vcls = g->d_vcls;
     a.nx = g->nx; a.ny = g->ny; a.V = g->V; a.B = g->B;
     a.G = scratch ? bp_groups(g) : 1;
     a.sidp = (float)(g->sid / g->pixel);
@@ -557,7 +584,7 @@ cudaError_t launch_backproject(const tnlm_geometry* g, const float* sino, float*
 // Allocation-free projection: the dual-layout scratch of K1 lives in a
 // file-scope device array instead of the handle's workspace.
 // ---------------------------------------------------------------------------
-constexpr size_t kStaticScratchFloats = (size_t)6 << 20;   // 24 MiB per device
+constexpr size_t kStaticScratchFloats = (size_t)12 << 20;  // 48 MiB per device
 static __device__ __align__(256) float g_proj_scratch[kStaticScratchFloats];
 
 size_t static_scratch_floats() { return kStaticScratchFloats; }

@@ -48,9 +48,13 @@ def rel_l2(a, b):
 
 RAGGED = synth.Geometry(nx=37, ny=29, pixel_mm=1.1, n_phases=3, n_views=7, n_bins=45,
                         bin_mm=1.3, sid_mm=500.0, sdd_mm=800.0)
+# a 110-degree fan: some views' rays change marching class twice
+WIDEFAN = synth.Geometry(nx=18, ny=14, pixel_mm=2.0, n_phases=3, n_views=8, n_bins=96,
+                         bin_mm=2.0, sid_mm=60.0, sdd_mm=100.0)
 GEOMS = {
     "tiny": synth.case("tiny").geom,
     "ragged": RAGGED,
+    "widefan": WIDEFAN,
     "small": synth.small_geometry(),
     "mid_a": synth.case("mid_a").geom,
     "large_b": synth.case("large_b").geom,
@@ -97,7 +101,7 @@ def test_all_ones_image_projects_to_chords(tn):
     np.testing.assert_allclose(host(out), ref, rtol=1e-5, atol=OP_MAX_TOL * ref.max())
 
 
-@pytest.mark.parametrize("name", ["tiny", "ragged", "mid_a"])
+@pytest.mark.parametrize("name", ["tiny", "ragged", "widefan", "mid_a"])
 def test_adjointness_on_gpu(tn, name):
     g = GEOMS[name]
     geo = tn.tnlm_create_geometry(g)
