@@ -1,21 +1,27 @@
 """Benchmark: 10-phase 4DCT slices reconstructed per second (TNLM, Sec. 2.2).
 
-One step reconstructs the three dose scenarios of the paper-scale slice
-(256 x 256 pixels of 1.5 mm, 10 phases, 512 bins of 1 mm, source-isocentre
-1000 mm, source-detector 1500 mm; d = 5, W = 11, K = 50 outer iterations,
-M1 = 3 CGLS steps, M2 = 5 Gauss-Jacobi sweeps):
-  (a) 360 views per phase at I0 = 1e4, (b) 60 views at I0 = 1e6,
-  (c) 60 views at I0 = 1e4
-i.e. three tnlm_reconstruct calls, so value = 3 * steps * ranks / time.
+Default workload (--workload large): one step reconstructs the four dose
+scenarios of the 512 x 512 slice (0.8 mm pixels, 10 phases, 888 bins of
+1 mm, source-isocentre 1000 mm, source-detector 1500 mm; d = 7, W = 15,
+K = 100 outer iterations, M1 = 3 CGLS steps, M2 = 5 Gauss-Jacobi sweeps):
+  (a) 360 views per phase at I0 = 5e3, (b) 90 views at I0 = 1e5,
+  (c) 360 views at I0 = 1e5, (d) 90 views at I0 = 5e3
+i.e. four tnlm_reconstruct calls, so value = 4 * steps * ranks / time.
+--workload mid times the three 256 x 256 scenarios (d = 5, W = 11, K = 50)
+instead; --workload batch the batched many-slice workload.
 
 Each reconstruction is the whole TNLM algorithm box: the initial image by
 FBP of all views (tnlm_fbp, step 1) followed by the K outer iterations
 (tnlm_reconstruct: the first one launch by launch with the dominant kernel
-class timed by CUDA events, the other K - 1 as graph replays).  Inputs are synthetic (seeded phantom, analytic line
-integrals, Poisson noise).  --impl reference times the FP64 CPU oracle
-instead, on a bounded sample of the same step.
+class timed by CUDA events, the other K - 1 as graph replays).  Inputs are
+synthetic (seeded phantom, analytic line integrals, Poisson noise).  After
+the timed steps the last timed result of every scenario with a stored FP64
+oracle result (tests/golden/large_<s>_k100.txt, same start and K) is
+compared with it at the stored pixel positions (relative L2).  --impl
+reference times the FP64 CPU oracle instead, on a bounded sample of the same
+step.
 
-Multi-GPU: slices are independent, so each rank reconstructs its own three
+Multi-GPU: slices are independent, so each rank reconstructs its own
 slices (weak scaling); ranks only meet for the barrier and the max-time
 reduction.
 """
@@ -39,10 +45,16 @@ from paper_1009_1351_gb300 import synth  # noqa: E402
 
 METRIC = "10-phase slices reconstructed/s at fixed accuracy; TNLM+projector % HBM roofline"
 UNIT = "slices/s"
-SCENARIOS = ("mid_a", "mid_b", "mid_c")
-WORKLOAD = ("256x256 px @1.5 mm, 10 phases, 512 bins @1 mm, SID 1000 / SDD 1500 mm; "
+WORKLOADS = {
+    "large": (("large_a", "large_b", "large_c", "large_d"),
+              "512x512 px @0.8 mm, 10 phases, 888 bins @1 mm, SID 1000 / SDD 1500 mm; "
+              "scenarios (a) 360 views I0=5e3, (b) 90 views I0=1e5, (c) 360 views I0=1e5, "
+              "(d) 90 views I0=5e3; d=7, W=15, K=100, M1=3, M2=5, mu_hat=0.5, h=0.014"),
+    "mid": (("mid_a", "mid_b", "mid_c"),
+            "256x256 px @1.5 mm, 10 phases, 512 bins @1 mm, SID 1000 / SDD 1500 mm; "
             "scenarios (a) 360 views I0=1e4, (b) 60 views I0=1e6, (c) 60 views I0=1e4; "
-            "d=5, W=11, K=50, M1=3, M2=5, mu_hat=0.5, h=0.01")
+            "d=5, W=11, K=50, M1=3, M2=5, mu_hat=0.5, h=0.01"),
+}
 
 
 def _peaks():
@@ -216,7 +228,8 @@ def run_gpu(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    cases = [synth.case(s) for s in SCENARIOS]
+    scenarios, workload = WORKLOADS[args.workload]
+    cases = [synth.case(s) for s in scenarios]
     slices = []
     for c in cases:
         d = synth.make_inputs(c)
@@ -296,6 +309,23 @@ def run_gpu(args):
         launches += sum(v["launches"] for v in r.values())
         tn.tnlm_profile_enable(s["geo"], ())
 
+    # accuracy of the last timed result of every scenario with a stored FP64
+    # oracle result (same FBP start, same K), at the stored pixel positions
+    accuracy = []
+    if rank == 0:
+        from tests.golden import make_golden
+        for s in slices:
+            gold = make_golden.read_large(s["case"].name)
+            if gold is None or s["case"].params.k_outer != make_golden.LARGE_K:
+                continue
+            pix = np.array([p[:3] for p in gold[1]], dtype=np.int64)
+            want = np.array([p[3] for p in gold[1]])
+            got = s["f"][pix[:, 0], pix[:, 1], pix[:, 2]].double().cpu().numpy()
+            accuracy.append({"case": s["case"].name, "samples": int(len(want)),
+                             "rel_l2_vs_fp64_oracle": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                             "max_abs": float(np.max(np.abs(got - want))),
+                             "tolerance": 1e-4})
+
     # end-to-end through the C ABI with host buffers (pinned), copies timed
     for s in slices:
         tn.tnlm_profile_read(s["geo"])
@@ -341,7 +371,7 @@ def run_gpu(args):
                 achieved = amt / (per_launch_ms / 1e3) / 1e12
                 peak = alu_peak_tops()
                 src = "derived: 152 SMs x 128 FP32 lanes x max SM clock (1 op per lane and clock)"
-            traffic = measured_traffic(dominant, SCENARIOS)
+            traffic = measured_traffic(dominant, scenarios)
             roof = {"bound": bound, "kernel": dominant, "achieved": round(achieved, 3),
                     "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
                     "traffic": None if traffic is None else int(traffic),
@@ -359,28 +389,29 @@ def run_gpu(args):
                 ach, pk = amt_c / (ms_c / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0)
             else:
                 ach, pk = amt_c / (ms_c / 1e3) / 1e12, alu_peak_tops()
-            tr = measured_traffic(cls, SCENARIOS)
+            tr = measured_traffic(cls, scenarios)
             by_kernel[cls] = {"bound": bound_c, "achieved": round(ach, 3), "peak": round(pk, 1),
                               "unit": unit_c, "frac": round(ach / pk, 4), "launch_ms": round(ms_c, 4),
                               "traffic": None if tr is None else int(tr)}
         out = {
-            "metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world,
+            "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded ellipse phantom, analytic line integrals, Poisson noise)",
-            "config": {"workload": WORKLOAD, "slices_per_step": n_slices,
+            "config": {"workload": workload, "slices_per_step": n_slices,
                        "l2": "flushed between steps (256 MiB write, untimed)",
                        "parity": "GPU FP32 vs FP64 oracle rel. L2 <= 1e-4 (tests/test_gpu_parity.py)",
                        "parallelism": f"replicas x{world}"},
+            "accuracy": accuracy,
             "clocks": clk, "gpu_launches": int(launches / args.steps),
-            "e2e": {"value": round(e2e_value, 4), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": round(e2e_value, 6), "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": roof,
             "roofline_by_kernel": by_kernel,
             "kernel_ms_share": {k: round(v / max(sum(prof.values()), 1e-9), 4) for k, v in prof.items()},
         }
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args.cpu_outer)
+            out["cpu_baseline"] = cpu_baseline(args.cpu_outer, scenarios, args.cpu_threads)
         print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()
@@ -469,58 +500,80 @@ def run_batch(args):
 # ---------------------------------------------------------------------------
 # CPU oracle (reported baseline, and the reference arm)
 # ---------------------------------------------------------------------------
-def _oracle_sample(k_outer: int):
-    """Time the FP64 oracle on k_outer outer iterations of each scenario and
-    extrapolate to the K = 50 of the workload: returns (slices/s, seconds, threads)."""
+def _oracle_time(name: str, k_outer: int):
+    """Time the FP64 oracle on one scenario: its FBP start and k_outer outer
+    iterations.  Returns (FBP seconds, seconds per outer iteration, K)."""
+    import oracle
+    c = synth.case(name)
+    d = synth.make_inputs(c)
+    G = oracle.Geom(c.geom)
+    p = synth.Params(**{**c.params.__dict__, "k_outer": k_outer})
+    y32, w32 = d["y"].astype(np.float32), d["w"].astype(np.float32)
+    t0 = time.perf_counter()
+    f0 = oracle.fbp(G, y32)
+    t1 = time.perf_counter()
+    oracle.reconstruct(G, y32, w32, f0, p)
+    t2 = time.perf_counter()
+    return t1 - t0, (t2 - t1) / k_outer, c.params.k_outer
+
+
+def _oracle_threads(n: int = 0) -> int:
     import oracle
     oracle.build()
-    nthreads = oracle.threads(os.cpu_count() or 1)
-    t_slice = 0.0
-    spent = 0.0
-    for s in SCENARIOS:
-        c = synth.case(s)
-        d = synth.make_inputs(c)
-        G = oracle.Geom(c.geom)
-        p = synth.Params(**{**c.params.__dict__, "k_outer": k_outer})
-        t0 = time.perf_counter()
-        f0 = oracle.fbp(G, d["y"])
-        t1 = time.perf_counter()
-        oracle.reconstruct(G, d["y"], d["w"], f0, p)
-        dt = time.perf_counter() - t1
-        spent += dt + (t1 - t0)
-        t_slice += (t1 - t0) + dt / k_outer * c.params.k_outer
-    return len(SCENARIOS) / t_slice, spent, nthreads
+    return oracle.threads(n if n > 0 else (os.cpu_count() or 1))
 
 
-def cpu_baseline(k_outer: int):
-    v, spent, n = _oracle_sample(k_outer)
-    return {"value": round(v, 6), "unit": UNIT, "cores": n, "kind": "oracle",
-            "sample": (f"FBP plus {k_outer} of the K=50 outer iterations of each of the 3 scenario "
-                       f"slices ({spent:.1f} s of FP64 oracle time on {n} threads), outer iterations "
-                       f"extrapolated linearly to K=50")}
+def cpu_baseline(k_outer: int, scenarios, threads: int = 0):
+    """The FP64 oracle on the host cores: the FBP and k_outer of the K outer
+    iterations of every scenario slice, outer iterations extrapolated
+    linearly to K (slices/s = slices / sum of the per-slice times)."""
+    n = _oracle_threads(threads)
+    spent, t_slices = 0.0, 0.0
+    for s in scenarios:
+        tf, ti, kk = _oracle_time(s, k_outer)
+        spent += tf + ti * k_outer
+        t_slices += tf + ti * kk
+    kk = synth.case(scenarios[0]).params.k_outer
+    return {"value": round(len(scenarios) / t_slices, 6), "unit": UNIT, "cores": n, "kind": "oracle",
+            "sample": (f"FBP plus {k_outer} of the K={kk} outer iterations of each of the "
+                       f"{len(scenarios)} scenario slices ({spent:.1f} s of FP64 oracle time on {n} "
+                       f"threads), outer iterations extrapolated linearly to K={kk}")}
 
 
 def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands on the host cores.  Step j
+    times scenario j mod S (its FBP and one outer iteration); the value is
+    S slices over the sum of the mean extrapolated per-slice times of the
+    scenarios measured.  Warm-up steps run one outer iteration of the tiny
+    64^2 workload."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    scenarios, workload = WORKLOADS[args.workload if args.workload in WORKLOADS else "large"]
+    n = _oracle_threads(args.cpu_threads)
     for _ in range(args.warmup):
-        _oracle_sample(1)
-    vals, spent_total, n = [], 0.0, 1
-    for _ in range(args.steps):
-        v, spent, n = _oracle_sample(1)
-        vals.append(v)
-        spent_total += spent
-    value = statistics.median(vals)
+        _oracle_time("tiny", 1)
+    per = {}
+    spent_total = 0.0
+    for j in range(args.steps):
+        name = scenarios[j % len(scenarios)]
+        tf, ti, kk = _oracle_time(name, 1)
+        spent_total += tf + ti
+        per.setdefault(name, []).append(tf + ti * kk)
+    t_sum = sum(statistics.mean(v) for v in per.values())
+    value = len(per) / t_sum
+    kk = synth.case(scenarios[0]).params.k_outer
+    sample = (f"per step: the FBP and 1 of the K={kk} outer iterations of one scenario slice "
+              f"(in turn: {', '.join(scenarios)}), extrapolated linearly to K={kk}; value = scenarios "
+              f"measured / sum of their mean per-slice times")
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": round(1e3 * spent_total / args.steps, 1), "higher_is_better": True,
+           "ms_per_step": round(1e3 * spent_total / max(args.steps, 1), 1), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "slices_per_step": 3},
+           "config": {"workload": workload, "slices_per_step": 1},
            "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": n, "kind": "oracle",
-                            "sample": "per step: FBP plus 1 of the K=50 outer iterations of each of "
-                                      "the 3 scenario slices, outer iterations extrapolated to K=50"},
+                            "sample": sample},
            "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -534,9 +587,12 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--cpu-outer", type=int, default=1,
                     help="outer iterations of the oracle per scenario for cpu_baseline")
+    ap.add_argument("--cpu-threads", type=int, default=0,
+                    help="oracle threads for cpu_baseline and the reference arm (0: all host cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=("slice", "batch"), default="slice",
-                    help="slice: the three 256^2 scenarios (default line); batch: many uneven slices")
+    ap.add_argument("--workload", choices=("large", "mid", "batch"), default="large",
+                    help="large: the four 512^2 scenarios (default line); mid: the three 256^2 "
+                         "scenarios; batch: many uneven slices")
     ap.add_argument("--batch-size", type=int, default=64)
     ap.add_argument("--precision", choices=("mixed", "fp32"), default="mixed",
                     help="patch distances of the batch workload")

@@ -9,6 +9,16 @@ W = 5, h = 0.006, mu_hat = 0.5, M1 = 3 CGLS steps, M2 = 5 Gauss-Jacobi
 sweeps, clamp), three outer iterations of the TNLM algorithm box from the
 constant start image 0.01: the relative change and data residual after
 every iteration and 96 pixel values at seeded positions.
+
+large_<s>_k100.txt: a 512 x 512 workload (0.8 mm pixels, 10 phases, 888
+bins of 1 mm, d = 7, W = 15, h = 0.014, mu_hat = 0.5, M1 = 3, M2 = 5,
+clamp; scenario a: 360 views per phase at I0 = 5e3, b: 90 views at
+I0 = 1e5), the full K = 100 outer iterations of the TNLM algorithm box from
+the oracle's own FBP of all views (box step 1): the relative change and data
+residual after every iteration and 8192 pixel values at seeded positions
+over the whole image.  At 8 host threads one file takes 30-60 minutes.
+
+    python tests/golden/make_golden.py large_a large_b
 """
 import os
 import sys
@@ -58,6 +68,54 @@ def write_tiny_k3(path=os.path.join(HERE, "tiny_k3.txt")):
             fh.write(f"pixel {i} {y} {x} {float(f[i, y, x])!r}\n")
 
 
+LARGE_K = 100
+LARGE_SAMPLES = 8192
+LARGE_SEED = 2718
+
+
+def large_positions(shape, n=LARGE_SAMPLES, seed=LARGE_SEED):
+    """Seeded positions anywhere in the [N][ny][nx] image."""
+    rng = np.random.default_rng(seed)
+    N, ny, nx = shape
+    return np.stack([rng.integers(0, N, n), rng.integers(0, ny, n), rng.integers(0, nx, n)], axis=1)
+
+
+def large_path(name):
+    return os.path.join(HERE, f"{name}_k{LARGE_K}.txt")
+
+
+def write_large(name):
+    """Full-length reconstruction of one 512^2 scenario from the oracle's FBP."""
+    import oracle
+    from paper_1009_1351_gb300 import synth
+    c = synth.case(name)
+    assert c.params.k_outer == LARGE_K
+    d = synth.make_inputs(c)
+    G = oracle.Geom(c.geom)
+    y32, w32 = d["y"].astype(np.float32), d["w"].astype(np.float32)
+    f0 = oracle.fbp(G, y32)
+    f, rel, res = oracle.reconstruct(G, y32, w32, f0, c.params)
+    pos = large_positions(f.shape)
+    with open(large_path(name), "w") as fh:
+        fh.write(f"# TNLM algorithm box, workload {name}, K = {LARGE_K} from the FBP of all views "
+                 "(FP64 oracle).\n")
+        fh.write("# Written by tests/golden/make_golden.py; see its docstring for the workload.\n")
+        fh.write(f"# norm {float(np.linalg.norm(f))!r}\n")
+        fh.write("# iter <k> <relative change> <data residual>\n")
+        fh.write("# pixel <phase> <row> <column> <value>\n")
+        for k in range(len(rel)):
+            fh.write(f"iter {k + 1} {float(rel[k])!r} {float(res[k])!r}\n")
+        for i, y, x in pos:
+            fh.write(f"pixel {i} {y} {x} {float(f[i, y, x])!r}\n")
+
+
+def read_large(name):
+    """(iters, pixels) of a stored 512^2 file, or None when it is missing."""
+    if not os.path.exists(large_path(name)):
+        return None
+    return read_tiny_k3(large_path(name))
+
+
 def read_tiny_k3(path=os.path.join(HERE, "tiny_k3.txt")):
     iters, pix = [], []
     for line in open(path):
@@ -74,5 +132,11 @@ def read_tiny_k3(path=os.path.join(HERE, "tiny_k3.txt")):
 if __name__ == "__main__":
     import oracle
     oracle.build()
-    write_tiny_k3()
-    print("wrote", os.path.join(HERE, "tiny_k3.txt"))
+    names = sys.argv[1:] or ["tiny"]
+    for nm in names:
+        if nm == "tiny":
+            write_tiny_k3()
+            print("wrote", os.path.join(HERE, "tiny_k3.txt"))
+        else:
+            write_large(nm)
+            print("wrote", large_path(nm))
