@@ -289,8 +289,8 @@ void tnlm_debug_fail_alloc_after(int n);
  * copies, waits (with the built-in limit) for the copies it has in flight,
  * leaves its outputs unwritten and sets the device flag that the next
  * synchronising call reports as TNLM_ERR_TIMEOUT; the handle stays usable.
- * Affects launches issued after the call (captured graphs keep the value
- * they were captured with). */
+ * Affects launches issued after the call: a cached graph of an outer
+ * iteration is re-captured when the limit it was captured with differs. */
 void tnlm_debug_wait_limit(long polls);
 
 #ifdef __cplusplus

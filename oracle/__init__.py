@@ -51,6 +51,8 @@ def _load():
         lib.orc_threads.restype = ctypes.c_int
         lib.orc_ray_entries.restype = ctypes.c_int
         lib.orc_objective_op.restype = ctypes.c_double
+        lib.orc_tnlm_term.restype = ctypes.c_double
+        lib.orc_data_term.restype = ctypes.c_double
         _lib = lib
     return _lib
 
@@ -188,6 +190,25 @@ def objective_op(G: Geom, y, w, f, wnext, W: int, mu: float) -> float:
     """Data term of Eq. 1 plus mu * sum_i [||f_i||^2 - <f_i, W_{i,i+1} f_{i+1}>]."""
     return float(_load().orc_objective_op(*G.args(), _d(_f64(y)), _d(_f64(w)), _d(_f64(f)),
                                           _d(_f64(wnext)), ctypes.c_int(W), ctypes.c_double(mu)))
+
+
+def tnlm_term(f, wnext, wprev, W: int) -> float:
+    """The bracket of Eq. 1 summed over phases: sum_i [J(f_i, f_{i-1}) + J(f_i, f_{i+1})]
+    with J of Eq. 2 and the weights laid out as ``weights`` returns them."""
+    f = _f64(f)
+    N, ny, nx = f.shape
+    return float(_load().orc_tnlm_term(ctypes.c_int(N), ctypes.c_int(nx), ctypes.c_int(ny),
+                                       ctypes.c_int(W), _d(f), _d(_f64(wnext)), _d(_f64(wprev))))
+
+
+def data_term(G: Geom, y, w, f) -> float:
+    """Data term of Eq. 1: sum_i (P_i f_i - y_i)^T Sigma^{-1} (P_i f_i - y_i)."""
+    return float(_load().orc_data_term(*G.args(), _d(_f64(y)), _d(_f64(w)), _d(_f64(f))))
+
+
+def objective(G: Geom, y, w, f, wnext, wprev, W: int, mu: float) -> float:
+    """Eq. 1: data term + (mu / 2) * sum_i [J(f_i, f_{i-1}) + J(f_i, f_{i+1})]."""
+    return data_term(G, y, w, f) + 0.5 * mu * tnlm_term(f, wnext, wprev, W)
 
 
 def fbp(G: Geom, y) -> np.ndarray:

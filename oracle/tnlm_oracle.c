@@ -23,6 +23,7 @@
  *   orc_fbp                         step 1 of the TNLM box: FBP of all views
  *   orc_objective_op                data term of Eq. 1 plus the TNLM energy
  *       whose exact prox the Gauss-Jacobi fixed point (Eq. 7) is.
+ *   orc_tnlm_term, orc_data_term    the two terms of Eq. 1 (J as Eq. 2).
  *
  * Readings where the paper is silent (kept identical on the CUDA side):
  *   - pixel squares are [c - d/2, c + d/2) on each axis; a segment is given
@@ -502,6 +503,54 @@ double orc_objective_op(const int* gi, const double* gd, const double* ang,
     }
     free(t);
     return data + mu * reg;
+}
+
+/* The bracket of Eq. 1 summed over phases, each J as Eq. 2 defines it:
+ *   T(f) = sum_i [ J(f_i, f_{i-1}) + J(f_i, f_{i+1}) ],
+ *   J(f_i, f_j) = sum_x sum_y [f_i(x) - f_j(y)]^2 omega_{i,j}(x, y),
+ * with omega_{i,i+1}(x, x+s) = wnext[i][x][s] and omega_{i,i-1}(x, x+s) =
+ * wprev[i][x][s] (rows over the W x W window, candidates outside the image
+ * carry no weight).  Eq. 1 is then data + (mu / 2) * T(f). */
+double orc_tnlm_term(int N, int nx, int ny, int W, const double* f, const double* wnext,
+                     const double* wprev)
+{
+    const int rho = (W - 1) / 2, W2 = W * W;
+    const long npx = (long)nx * ny;
+    double tot = 0.0;
+    for (int i = 0; i < N; ++i) {
+        const double* fi = f + (long)i * npx;
+        for (int dir = 0; dir < 2; ++dir) {
+            const int j = dir == 0 ? (i + N - 1) % N : (i + 1) % N;
+            const double* fj = f + (long)j * npx;
+            const double* w = dir == 0 ? wprev : wnext;
+            double J = 0.0;
+            for (long p = 0; p < npx; ++p) {
+                int x = (int)(p % nx), yy = (int)(p / nx);
+                for (int sy = -rho; sy <= rho; ++sy)
+                    for (int sx = -rho; sx <= rho; ++sx) {
+                        int x1 = x + sx, y1 = yy + sy;
+                        if (x1 < 0 || x1 >= nx || y1 < 0 || y1 >= ny) continue;
+                        double dv = fi[p] - fj[(long)y1 * nx + x1];
+                        J += dv * dv * w[((long)i * npx + p) * W2 + (sy + rho) * W + (sx + rho)];
+                    }
+            }
+            tot += J;
+        }
+    }
+    return tot;
+}
+
+/* Data term of Eq. 1: sum_i (P_i f_i - y_i)^T Sigma^{-1} (P_i f_i - y_i). */
+double orc_data_term(const int* gi, const double* gd, const double* ang, const double* y,
+                     const double* w, const double* f)
+{
+    const long NS = (long)NPH * NV * NB;
+    double* t = (double*)malloc(sizeof(double) * NS);
+    orc_project(gi, gd, ang, f, t);
+    double data = 0.0;
+    for (long k = 0; k < NS; ++k) data += w[k] * (t[k] - y[k]) * (t[k] - y[k]);
+    free(t);
+    return data;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -217,6 +217,7 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     }
     char* b = (char*)base;
     ws = Workspace{};
+    g->ws_gen++;
     ws.base = base;
     ws.bytes = L.total;
     ws.rho = nrho;
@@ -334,14 +335,16 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
 // One outer iteration captured as a CUDA graph on a handle-owned stream and
 // replayed on the caller's stream.  The key is everything the captured
 // launches depend on: the parameters that shape them, the caller's y and f
-// pointers and the workspace allocation.
+// pointers, the workspace allocation (by generation, not address), the
+// launch tuning and the sweep's wait limit (a kernel argument).
 struct GraphState {
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
     tnlm_params p{};
     const float* y = nullptr;
     float* f = nullptr;
-    void* ws = nullptr;
+    unsigned long long ws_gen = 0;
+    long wait_limit = 0;
     unsigned tune_gen = 0;
     long long launches[TNLM_KCLASS_COUNT] = {0, 0, 0, 0, 0, 0};  // kernels per replay
 };
@@ -355,8 +358,8 @@ bool same_shape(const tnlm_params& a, const tnlm_params& b) {
 tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f) {
     GraphState* G = (GraphState*)g->graph;
     if (!G) g->graph = G = new GraphState();
-    if (G->exec && G->y == d_y && G->f == d_f && G->ws == g->ws.base && same_shape(G->p, *p) &&
-        G->tune_gen == g->tune_gen)
+    if (G->exec && G->y == d_y && G->f == d_f && G->ws_gen == g->ws_gen && same_shape(G->p, *p) &&
+        G->tune_gen == g->tune_gen && G->wait_limit == g_gj_wait_limit)
         return TNLM_OK;
     if (G->exec) {
         cudaGraphExecDestroy(G->exec);
@@ -390,7 +393,8 @@ tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_
     G->p = *p;
     G->y = d_y;
     G->f = d_f;
-    G->ws = g->ws.base;
+    G->ws_gen = g->ws_gen;
+    G->wait_limit = g_gj_wait_limit;
     G->tune_gen = g->tune_gen;
     return TNLM_OK;
 }
@@ -558,13 +562,14 @@ __global__ void k_batch_gate(const GateSlice* __restrict__ s, const cudaGraphCon
 struct BatchItem {
     unsigned long long uid;
     unsigned tune_gen;
-    void* ws;
+    unsigned long long ws_gen;
+    long wait_limit;
     const float* y;
     float* f;
     tnlm_params p;
     bool operator==(const BatchItem& o) const {
-        return uid == o.uid && tune_gen == o.tune_gen && ws == o.ws && y == o.y && f == o.f &&
-               same_shape(p, o.p);
+        return uid == o.uid && tune_gen == o.tune_gen && ws_gen == o.ws_gen &&
+               wait_limit == o.wait_limit && y == o.y && f == o.f && same_shape(p, o.p);
     }
 };
 
@@ -666,7 +671,7 @@ tnlm_status loop_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
     const size_t n = gs.size();
     std::vector<BatchItem> key(n);
     for (size_t j = 0; j < n; ++j)
-        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws.base, ys[j], fs[j], *ps[j]};
+        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws_gen, g_gj_wait_limit, ys[j], fs[j], *ps[j]};
     if (B->loop_exec && key == B->loop_key) {
         *built = true;
         return TNLM_OK;
@@ -758,7 +763,7 @@ tnlm_status batch_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
                         const std::vector<float*>& fs) {
     std::vector<BatchItem> key(gs.size());
     for (size_t j = 0; j < gs.size(); ++j)
-        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws.base, ys[j], fs[j], *ps[j]};
+        key[j] = {gs[j]->uid, gs[j]->tune_gen, gs[j]->ws_gen, g_gj_wait_limit, ys[j], fs[j], *ps[j]};
     if (B->exec && key == B->key) return TNLM_OK;
     if (B->exec) {
         cudaGraphExecDestroy(B->exec);

@@ -100,6 +100,11 @@ struct tnlm_geometry {
                                 // and of the row-marching rays (z, w) of each view; lo > hi: none
     float* d_fbp_taps = nullptr; // [2B-1] discrete equiangular ramp kernel of the initial FBP
     tnlm::Workspace ws;
+    // changes whenever ensure_ws replaces the workspace allocation: the
+    // buffer offsets depend on the window radius and history capacity it
+    // was sized for, and a new allocation may reuse a freed address, so
+    // captured graphs are keyed on this counter rather than on the address
+    unsigned long long ws_gen = 0;
     int cta_slots_bp = 0;       // resident backprojector CTAs on the device
     int cta_slots_gj = 0;       // resident TMA-sweep CTAs on the device
     int num_sms = 0;            // streaming multiprocessors of the device

@@ -131,3 +131,53 @@ def test_sweep_wait_timeout_is_reported_and_the_handle_recovers(tn, case):
     torch.cuda.synchronize()
     assert rep["iterations"] == 1
     assert torch.equal(a, b)
+
+
+def test_wait_limit_applies_to_cached_graphs(tn, case):
+    """A reconstruction with K > 1 replays a captured graph of one outer
+    iteration; the sweep's wait limit is a kernel argument, so lowering it
+    must re-capture (every replay then times out) and restoring it must
+    re-capture again (the handle then matches a fresh one bitwise)."""
+    c, y, w, f0 = case
+    p = synth.Params(**{**c.params.__dict__, "k_outer": 3})
+    geo = tn.tnlm_create_geometry(c.geom)
+    tn.tnlm_reconstruct(geo, p, y, w, f0.clone())          # graph captured with the normal limit
+    tn.tnlm_debug_wait_limit(0)
+    try:
+        with pytest.raises(tn.TnlmError) as e:
+            tn.tnlm_reconstruct(geo, p, y, w, f0.clone())
+    finally:
+        tn.tnlm_debug_wait_limit(-1)
+    assert e.value.status == tn.TNLM_ERR_TIMEOUT
+    a = f0.clone()
+    tn.tnlm_reconstruct(geo, p, y, w, a)
+    b = f0.clone()
+    tn.tnlm_reconstruct(tn.tnlm_create_geometry(c.geom), p, y, w, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+def test_cached_graph_follows_workspace_reallocation(tn, case):
+    """The weights call with a wider window grows (re-allocates) the
+    handle's workspace, whose buffer offsets depend on the window; a later
+    reconstruction with the first parameters must not replay the graph
+    captured on the old layout, even if the new allocation reuses its
+    address."""
+    c, y, w, f0 = case
+    p = synth.Params(**{**c.params.__dict__, "k_outer": 3})
+    geo = tn.tnlm_create_geometry(c.geom)
+    tn.tnlm_reconstruct(geo, p, y, w, f0.clone())
+    N, ny, nx = f0.shape
+    for W in (9, 11):
+        q = synth.Params(**{**c.params.__dict__, "window": W})
+        nd, nn = tn.tnlm_weights_size(geo, q)
+        dist = torch.empty(nd // 4, device="cuda")
+        norm = torch.empty(nn // 4, device="cuda")
+        tn.tnlm_weights(geo, q, f0, dist, norm)
+        del dist, norm
+    a = f0.clone()
+    tn.tnlm_reconstruct(geo, p, y, w, a)
+    b = f0.clone()
+    tn.tnlm_reconstruct(tn.tnlm_create_geometry(c.geom), p, y, w, b)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
