@@ -91,19 +91,38 @@ typedef struct {
                         TNLM_PREC_MIXED: the patch-distance cross terms of Eq. 8 as
                         split-FP16 tensor-core products with FP32 accumulation
                         (patch <= 5, window <= 11), all else as FP32 */
+    int monitor;     /* 1: every outer iteration also reduces, in FP64, the TNLM term
+                        of Eq. 1 (J of Eq. 2 toward both neighbours, with that
+                        iteration's weights, at the iteration's result), and the call
+                        ends with one more projection for the data term of the final
+                        image (see tnlm_report); costs one more pass over the stored
+                        distances per iteration.  0: off */
 } tnlm_params;
 
 enum { TNLM_PREC_FP32 = 0, TNLM_PREC_MIXED = 1 };
 
 /* Host-side report of tnlm_reconstruct (all FP64 values come from FP64
- * device reductions). */
+ * device reductions).  Every *_hist pointer is an optional caller-owned host
+ * array of k_outer entries (entry k: outer iteration k + 1) or NULL. */
 typedef struct {
     int iterations;          /* outer iterations executed */
     double rel_change;       /* ||f^k - f^(k-1)||_2 / ||f^k||_2 of the last one */
     double data_residual;    /* sum_i ||Sigma^{-1/2}(P_i f_i - y_i)||^2 at the start of
                                 the last outer iteration (i.e. of f^(k-1)) */
-    double* rel_change_hist; /* optional caller-owned host array [k_outer] or NULL */
-    double* residual_hist;   /* optional caller-owned host array [k_outer] or NULL */
+    double* rel_change_hist;
+    double* residual_hist;
+    long long clamped;       /* pixels the positivity step (TNLM box step 5) set to 0 in
+                                the last outer iteration (0 with clamp = 0) */
+    long long* clamped_hist;
+    /* with params.monitor = 1 (otherwise the scalars are 0 and the arrays untouched): */
+    double tnlm_term;        /* T(f^k) = sum_i [J(f_i, f_{i-1}) + J(f_i, f_{i+1})] (Eq. 2) at
+                                the last result, with the last iteration's weights */
+    double objective;        /* Eq. 1 at the last result: data term + (mu / 2) T, with
+                                mu = mu_hat * beta (Eq. 7; with beta = 0, as the CGLS data
+                                step allows, this is the data term alone) */
+    double* tnlm_hist;       /* T after every iteration */
+    double* data_hist;       /* data term of the image after every iteration */
+    double* objective_hist;  /* Eq. 1 after every iteration */
 } tnlm_report;
 
 /* Create a geometry handle on desc->device.  The library copies the view

@@ -50,14 +50,41 @@ class ParamsC(ctypes.Structure):
                 ("patch", ctypes.c_int), ("window", ctypes.c_int), ("m1", ctypes.c_int),
                 ("m2", ctypes.c_int), ("k_outer", ctypes.c_int), ("data_step", ctypes.c_int),
                 ("clamp", ctypes.c_int), ("tol", ctypes.c_double),
-                ("tol_check_every", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("tol_check_every", ctypes.c_int), ("precision", ctypes.c_int),
+                ("monitor", ctypes.c_int)]
 
 
 class ReportC(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("rel_change", ctypes.c_double),
                 ("data_residual", ctypes.c_double),
                 ("rel_change_hist", ctypes.POINTER(ctypes.c_double)),
-                ("residual_hist", ctypes.POINTER(ctypes.c_double))]
+                ("residual_hist", ctypes.POINTER(ctypes.c_double)),
+                ("clamped", ctypes.c_longlong),
+                ("clamped_hist", ctypes.POINTER(ctypes.c_longlong)),
+                ("tnlm_term", ctypes.c_double), ("objective", ctypes.c_double),
+                ("tnlm_hist", ctypes.POINTER(ctypes.c_double)),
+                ("data_hist", ctypes.POINTER(ctypes.c_double)),
+                ("objective_hist", ctypes.POINTER(ctypes.c_double))]
+
+
+def _new_report(k_outer: int):
+    """A ReportC with history arrays for k_outer iterations (kept alive by the tuple)."""
+    k = max(int(k_outer), 1)
+    arrs = [(ctypes.c_double * k)() for _ in range(5)] + [(ctypes.c_longlong * k)()]
+    rep = ReportC(0, 0.0, 0.0, arrs[0], arrs[1], 0, arrs[5], 0.0, 0.0, arrs[2], arrs[3], arrs[4])
+    return rep, arrs
+
+
+def _report_dict(rep, arrs, monitor: bool):
+    n = rep.iterations
+    out = {"iterations": n, "rel_change": rep.rel_change, "data_residual": rep.data_residual,
+           "rel_change_hist": list(arrs[0][:n]), "residual_hist": list(arrs[1][:n]),
+           "clamped": int(rep.clamped), "clamped_hist": [int(v) for v in arrs[5][:n]]}
+    if monitor:
+        out.update({"tnlm_term": rep.tnlm_term, "objective": rep.objective,
+                    "tnlm_hist": list(arrs[2][:n]), "data_hist": list(arrs[3][:n]),
+                    "objective_hist": list(arrs[4][:n])})
+    return out
 
 
 class TnlmError(RuntimeError):
@@ -166,7 +193,7 @@ def params_c(p: Any) -> ParamsC:
                    int(p.window), int(p.m1), int(p.m2), int(p.k_outer),
                    int(getattr(p, "data_step", 0)), int(getattr(p, "clamp", 1)),
                    float(getattr(p, "tol", 0.0)), int(getattr(p, "tol_check_every", 1)),
-                   int(getattr(p, "precision", PREC_FP32)))
+                   int(getattr(p, "precision", PREC_FP32)), int(getattr(p, "monitor", 0)))
 
 
 class Geometry:
@@ -259,22 +286,18 @@ def tnlm_reconstruct(geom: Geometry, params, y, winv, f, report: bool = True,
                      stream=None) -> Optional[Dict[str, Any]]:
     """Run the TNLM iteration in place on f.  With report=True the call
     synchronises and returns the report (iterations, final relative change,
-    data residual and their per-iteration histories)."""
+    data residual, clamped pixels and their per-iteration histories; with
+    params.monitor = 1 also the TNLM term, data term and Eq. 1 objective)."""
     pc = params_c(params)
     lib = load_library()
     if not report:
         _check(lib.tnlm_reconstruct(geom.handle, ctypes.byref(pc), _ptr(y), _ptr(winv), _ptr(f),
                                     None, _stream(stream)))
         return None
-    k = max(int(pc.k_outer), 1)
-    rel = (ctypes.c_double * k)()
-    res = (ctypes.c_double * k)()
-    rep = ReportC(0, 0.0, 0.0, rel, res)
+    rep, arrs = _new_report(pc.k_outer)
     _check(lib.tnlm_reconstruct(geom.handle, ctypes.byref(pc), _ptr(y), _ptr(winv), _ptr(f),
                                 ctypes.byref(rep), _stream(stream)))
-    n = rep.iterations
-    return {"iterations": n, "rel_change": rep.rel_change, "data_residual": rep.data_residual,
-            "rel_change_hist": list(rel[:n]), "residual_hist": list(res[:n])}
+    return _report_dict(rep, arrs, bool(pc.monitor))
 
 
 def tnlm_autotune(geom: Geometry, params, y, winv, f0, stream=None) -> Dict[str, int]:
@@ -309,19 +332,12 @@ def tnlm_reconstruct_batch(geoms, params, ys, winvs, fs, autotune: bool = True,
     hist = []
     reps = (ReportC * n)()
     for k in range(n):
-        kk = max(int(pcs[k].k_outer), 1)
-        rel, res = (ctypes.c_double * kk)(), (ctypes.c_double * kk)()
-        hist.append((rel, res))
-        reps[k] = ReportC(0, 0.0, 0.0, rel, res)
+        rep, arrs = _new_report(pcs[k].k_outer)
+        hist.append(arrs)
+        reps[k] = rep
     _check(load_library().tnlm_reconstruct_batch(hs, pcs, n, yp, wp, fp, reps, 1 if autotune else 0,
                                                  _stream(stream)))
-    out = []
-    for k in range(n):
-        m = reps[k].iterations
-        out.append({"iterations": m, "rel_change": reps[k].rel_change,
-                    "data_residual": reps[k].data_residual,
-                    "rel_change_hist": list(hist[k][0][:m]), "residual_hist": list(hist[k][1][:m])})
-    return out
+    return [_report_dict(reps[k], hist[k], bool(pcs[k].monitor)) for k in range(n)]
 
 
 def tnlm_batch_last_was_loop() -> bool:

@@ -141,6 +141,7 @@ tnlm_status check_params(const tnlm_params* p) {
         return fail(TNLM_ERR_INVALID_ARG, "precision must be TNLM_PREC_FP32 or TNLM_PREC_MIXED");
     if (p->precision == TNLM_PREC_MIXED && !weights_tc_supported(p->patch, p->window))
         return fail(TNLM_ERR_INVALID_ARG, "mixed precision supports patch <= 5 and window in [3, 11]");
+    if (p->monitor != 0 && p->monitor != 1) return fail(TNLM_ERR_INVALID_ARG, "monitor must be 0 or 1");
     return TNLM_OK;
 }
 
@@ -149,7 +150,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Byte layout of the workspace for window radius rho and history capacity kcap.
 struct WsLayout {
     size_t off_u, off_s, off_s2, off_gr, off_R, off_T, off_r, off_z, off_t, off_sw, off_bps, off_D, off_U0, off_U1,
-        off_mins, off_zn, off_part, off_part2, off_gjs, off_gjc, off_state, total;
+        off_mins, off_zn, off_part, off_part2, off_part3, off_gjs, off_gjc, off_state, total;
     size_t part_len, part2_len;
     PadPlane pp;
 };
@@ -187,13 +188,15 @@ WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
     L.off_mins = take(4 * 2 * npx * N);
     L.off_zn = take(4 * 2 * npx * N);
     L.part_len = N * (size_t)g->V * proj_chunks(g) + N * (size_t)bp_blocks_per_phase(g);
-    L.part2_len = 2 * (size_t)gj_blocks(g);
+    L.part2_len = 3 * (size_t)gj_blocks(g);
     L.off_part = take(8 * L.part_len);
     L.off_part2 = take(8 * L.part2_len);
+    L.off_part3 = take(8 * (size_t)tnlm_energy_blocks(g));
     L.off_gjs = take(4 * gj_split_floats(g));
     L.off_gjc = take(4 * (size_t)gj_blocks(g));
-    // state: gamma, a, b, res0 [N] doubles; hist 2 x kcap doubles; active [N], iter, err ints
-    L.off_state = take(8 * (4 * N + 2 * (size_t)kcap) + 4 * (N + 2));
+    // state: gamma, a, b, res0 [N] doubles; hist 4 x kcap doubles; res_final;
+    // active [N], iter, err ints
+    L.off_state = take(8 * (4 * N + 4 * (size_t)kcap + 1) + 4 * (N + 2));
     L.total = o;
     return L;
 }
@@ -242,6 +245,7 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     ws.part = (double*)(b + L.off_part);
     ws.part_len = L.part_len;
     ws.part2 = (double*)(b + L.off_part2);
+    ws.part3 = (double*)(b + L.off_part3);
     ws.gjsum = (float*)(b + L.off_gjs);
     ws.gjcnt = (int*)(b + L.off_gjc);
     const size_t N = g->N;
@@ -252,7 +256,10 @@ tnlm_status ensure_ws(tnlm_geometry* g, int rho, int kcap, cudaStream_t st) {
     ws.st.res0 = sd + 3 * N;
     ws.st.hist_rel = sd + 4 * N;
     ws.st.hist_res = sd + 4 * N + ws.kcap;
-    int* si = (int*)(sd + 4 * N + 2 * (size_t)ws.kcap);
+    ws.st.hist_clamp = sd + 4 * N + 2 * (size_t)ws.kcap;
+    ws.st.hist_tnlm = sd + 4 * N + 3 * (size_t)ws.kcap;
+    ws.st.res_final = sd + 4 * N + 4 * (size_t)ws.kcap;
+    int* si = (int*)(sd + 4 * N + 4 * (size_t)ws.kcap + 1);
     ws.st.active = si;
     ws.st.iter = si + N;
     ws.st.err = si + N + 1;
@@ -312,11 +319,13 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
         }
     }
     // ---- TNLM step: weights from g = ws.u, Gauss-Jacobi, positivity
-    if (p->m2 > 0) {
+    if (p->m2 > 0 || p->monitor) {
         if (p->precision == TNLM_PREC_MIXED)
             LK(TNLM_KCLASS_WEIGHTS, launch_weights_tc(g, ws, p->patch, p->window, ws.u, st), "weights (tensor cores)");
         else
             LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, ws, p->patch, p->window, ws.u, st), "weights");
+    }
+    if (p->m2 > 0) {
         float* bufs[2] = {ws.U0, ws.U1};
         for (int m = 0; m < p->m2; ++m) {
             const bool last = m == p->m2 - 1;
@@ -328,7 +337,22 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     } else {
         LK(TNLM_KCLASS_GJ, launch_finalize_nogj(g, ws, ws.u, d_f, p->clamp, st), "finalize");
     }
-    LK(TNLM_KCLASS_CGLS, launch_iter_scalars(g, ws, gj_blocks(g), st), "monitors");
+    if (p->monitor)
+        LK(TNLM_KCLASS_CGLS, launch_tnlm_energy(g, ws, p->window, p->h, d_f, st), "TNLM term monitor");
+    LK(TNLM_KCLASS_CGLS, launch_iter_scalars(g, ws, gj_blocks(g), p->monitor != 0, st), "monitors");
+    return TNLM_OK;
+}
+
+// Monitor: the data term of the final image, ||sqrt(w)(y - P f)||^2, into
+// st.res_final (one more projection after the last outer iteration).
+tnlm_status final_data_term(tnlm_geometry* g, const float* d_y, const float* d_f, cudaStream_t st) {
+    Workspace& ws = g->ws;
+    LK(TNLM_KCLASS_PREP, launch_prep_dual(g, d_f, ws.R, ws.T, st), "prep");
+    ProjOut o{};
+    o.mode = 1; o.r = ws.r; o.z = ws.z; o.y = d_y; o.sw = ws.sw; o.part = ws.part;
+    LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, o, st), "project");
+    LK(TNLM_KCLASS_CGLS, launch_sum_partials(ws.part, g->N * g->V * proj_chunks(g), ws.st.res_final, st),
+       "data term");
     return TNLM_OK;
 }
 
@@ -352,7 +376,7 @@ struct GraphState {
 bool same_shape(const tnlm_params& a, const tnlm_params& b) {
     return a.mu_hat == b.mu_hat && a.h == b.h && a.beta == b.beta && a.patch == b.patch &&
            a.window == b.window && a.m1 == b.m1 && a.m2 == b.m2 && a.data_step == b.data_step &&
-           a.clamp == b.clamp && a.precision == b.precision;
+           a.clamp == b.clamp && a.precision == b.precision && a.monitor == b.monitor;
 }
 
 tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f) {
@@ -793,25 +817,48 @@ tnlm_status batch_graph(BatchState* B, const std::vector<tnlm_geometry*>& gs,
 
 // Copies the monitors of the last reconstruction of g into rep and returns
 // the status its device flags call for (flags are cleared).
-tnlm_status read_report(tnlm_geometry* g, int done, tnlm_report* rep, cudaStream_t st) {
+tnlm_status read_report(tnlm_geometry* g, const tnlm_params* p, int done, tnlm_report* rep,
+                        cudaStream_t st) {
     Workspace& ws = g->ws;
     int err = 0;
     CK(cudaMemcpyAsync(&err, ws.st.err, sizeof(int), cudaMemcpyDeviceToHost, st), "readback");
-    std::vector<double> hrel(done > 0 ? done : 1), hres(done > 0 ? done : 1);
+    const size_t n = done > 0 ? (size_t)done : 1;
+    std::vector<double> hrel(n), hres(n), hcl(n), htn(n);
+    double rfin = 0.0;
     if (done > 0) {
         CK(cudaMemcpyAsync(hrel.data(), ws.st.hist_rel, sizeof(double) * done, cudaMemcpyDeviceToHost,
                            st), "readback");
         CK(cudaMemcpyAsync(hres.data(), ws.st.hist_res, sizeof(double) * done, cudaMemcpyDeviceToHost,
                            st), "readback");
+        CK(cudaMemcpyAsync(hcl.data(), ws.st.hist_clamp, sizeof(double) * done, cudaMemcpyDeviceToHost,
+                           st), "readback");
+        CK(cudaMemcpyAsync(htn.data(), ws.st.hist_tnlm, sizeof(double) * done, cudaMemcpyDeviceToHost,
+                           st), "readback");
+        if (p->monitor)
+            CK(cudaMemcpyAsync(&rfin, ws.st.res_final, sizeof(double), cudaMemcpyDeviceToHost, st),
+               "readback");
     }
     CK(cudaStreamSynchronize(st), "sync");
     if (rep) {
+        // mu of Eq. 1 is mu_hat * beta (Eq. 7); the data term of the image
+        // after iteration k is the residual the next iteration starts from
+        const double mu = p->mu_hat * p->beta;
         rep->iterations = done;
         rep->rel_change = done > 0 ? hrel[done - 1] : 0.0;
         rep->data_residual = done > 0 ? hres[done - 1] : 0.0;
+        rep->clamped = done > 0 ? (long long)hcl[done - 1] : 0;
+        rep->tnlm_term = done > 0 && p->monitor ? htn[done - 1] : 0.0;
+        rep->objective = done > 0 && p->monitor ? rfin + 0.5 * mu * htn[done - 1] : 0.0;
         for (int k = 0; k < done; ++k) {
+            const double dk = k + 1 < done ? hres[k + 1] : rfin;
             if (rep->rel_change_hist) rep->rel_change_hist[k] = hrel[k];
             if (rep->residual_hist) rep->residual_hist[k] = hres[k];
+            if (rep->clamped_hist) rep->clamped_hist[k] = (long long)hcl[k];
+            if (p->monitor) {
+                if (rep->tnlm_hist) rep->tnlm_hist[k] = htn[k];
+                if (rep->data_hist) rep->data_hist[k] = dk;
+                if (rep->objective_hist) rep->objective_hist[k] = dk + 0.5 * mu * htn[k];
+            }
         }
     }
     if (err) {
@@ -1218,7 +1265,11 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* gc, const tnlm_params* p, cons
             if (rel < p->tol) break;
         }
     }
-    if (sync) return read_report(g, done, rep, st);
+    if (p->monitor && done > 0) {
+        s = final_data_term(g, d_y, d_f, st);
+        if (s != TNLM_OK) return s;
+    }
+    if (sync) return read_report(g, p, done, rep, st);
     return TNLM_OK;
 }
 
@@ -1352,7 +1403,13 @@ tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_param
     }
     tnlm_status first = TNLM_OK;
     for (int i = 0; i < count; ++i) {
-        tnlm_status s = read_report(geoms[i], done[i], reports ? &reports[i] : nullptr, st);
+        if (params[i].monitor && done[i] > 0) {
+            tnlm_status s = final_data_term(geoms[i], d_y[i], d_f[i], st);
+            if (s != TNLM_OK) return s;
+        }
+    }
+    for (int i = 0; i < count; ++i) {
+        tnlm_status s = read_report(geoms[i], &params[i], done[i], reports ? &reports[i] : nullptr, st);
         if (s != TNLM_OK && first == TNLM_OK) first = s;
     }
     return first;

@@ -47,6 +47,9 @@ struct DevState {
     int* active;       // [N] CGLS not stopped
     double* hist_rel;  // [kcap]
     double* hist_res;  // [kcap]
+    double* hist_clamp; // [kcap] pixels clamped by the positivity step
+    double* hist_tnlm; // [kcap] TNLM term of Eq. 1 (monitor on)
+    double* res_final; // data term of the final image (monitor on)
     int* iter;         // outer iteration counter (device)
     int* err;          // numeric fault flag
 };
@@ -73,7 +76,8 @@ struct Workspace {
     // reductions
     double* part = nullptr;  // partial sums
     size_t part_len = 0;
-    double* part2 = nullptr; // second partial array (relative change)
+    double* part2 = nullptr; // second partial array (relative change, clamp count)
+    double* part3 = nullptr; // monitor partials (TNLM term per sweep block)
     float* gjsum = nullptr;  // TMA sweep: partial sums of window halves [tile][2][4][256] float4
     int* gjcnt = nullptr;    // TMA sweep: halves done per tile (0 between sweeps)
     DevState st{};
@@ -186,8 +190,13 @@ cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int win
                             float* fout, int clamp, cudaStream_t st);
 cudaError_t launch_finalize_nogj(const tnlm_geometry* g, const Workspace& ws, const float* gimg,
                                  float* fout, int clamp, cudaStream_t st);
-cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks,
+cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks, bool monitor,
                                 cudaStream_t st);
+// monitor: TNLM term of Eq. 1 from the stored distances and the result f
+cudaError_t launch_tnlm_energy(const tnlm_geometry* g, const Workspace& ws, int window, double h,
+                               const float* f, cudaStream_t st);
+int tnlm_energy_blocks(const tnlm_geometry* g);
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st);
 int gj_blocks(const tnlm_geometry* g);
 int gj_tma_split(const tnlm_geometry* g);
 // Poll limit of the TMA sweep's pipeline waits (not of its final drain);

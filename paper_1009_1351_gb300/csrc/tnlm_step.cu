@@ -293,6 +293,10 @@ cudaError_t launch_weights(const tnlm_geometry* g, const Workspace& ws, int patc
 // ---------------------------------------------------------------------------
 // K5
 // ---------------------------------------------------------------------------
+// Partial slots per block of the last sweep: squared change, squared norm,
+// clamped pixels.
+constexpr int kPart = 3;
+
 struct GjArgs {
     const float* D;
     const float* mins;
@@ -369,9 +373,10 @@ __global__ void __launch_bounds__(kGjTileX * kGjTileY) k_gj(GjArgs a) {
         if (in) a.uout[i * a.pp.plane + (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox] = unew;
         return;
     }
-    float fnew = 0.f, dif = 0.f;
+    float fnew = 0.f, dif = 0.f, ncl = 0.f;
     if (in) {
         fnew = a.clamp ? fmaxf(unew, 0.f) : unew;
+        ncl = (a.clamp && unew < 0.f) ? 1.f : 0.f;
         const float fold = a.fout[i * npx + pix];
         a.fout[i * npx + pix] = fnew;
         dif = fnew - fold;
@@ -379,9 +384,11 @@ __global__ void __launch_bounds__(kGjTileX * kGjTileY) k_gj(GjArgs a) {
     __shared__ double sh[kGjTileX * kGjTileY / 32];
     const double d2 = block_sum<kGjTileX * kGjTileY>(dif * dif, sh, tid);
     const double n2 = block_sum<kGjTileX * kGjTileY>(fnew * fnew, sh, tid);
+    const double c2 = block_sum<kGjTileX * kGjTileY>(ncl, sh, tid);
     if (tid == 0) {
-        a.part[2 * (size_t)blockIdx.x] = d2;
-        a.part[2 * (size_t)blockIdx.x + 1] = n2;
+        a.part[kPart * (size_t)blockIdx.x] = d2;
+        a.part[kPart * (size_t)blockIdx.x + 1] = n2;
+        a.part[kPart * (size_t)blockIdx.x + 2] = c2;
     }
 }
 
@@ -468,7 +475,7 @@ __global__ void __launch_bounds__(kGjvTx * kGjvTy) k_gj_vec(GjArgs a) {
             }
         }
     }
-    float dsq = 0.f, nsq = 0.f;
+    float dsq = 0.f, nsq = 0.f, ncl = 0.f;
     bool bad = false;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
@@ -486,6 +493,7 @@ __global__ void __launch_bounds__(kGjvTx * kGjvTy) k_gj_vec(GjArgs a) {
             a.uout[i * a.pp.plane + (size_t)(y + a.pp.oy) * px + x + a.pp.ox] = unew;
         } else {
             const float fnew = a.clamp ? fmaxf(unew, 0.f) : unew;
+            if (a.clamp && unew < 0.f) ncl += 1.f;
             const float fold = a.fout[i * npx + pix];
             a.fout[i * npx + pix] = fnew;
             dsq = fmaf(fnew - fold, fnew - fold, dsq);
@@ -497,9 +505,11 @@ __global__ void __launch_bounds__(kGjvTx * kGjvTy) k_gj_vec(GjArgs a) {
         __shared__ double sh[kGjvTx * kGjvTy / 32];
         const double d2 = block_sum<kGjvTx * kGjvTy>(dsq, sh, tid);
         const double n2 = block_sum<kGjvTx * kGjvTy>(nsq, sh, tid);
+        const double c2 = block_sum<kGjvTx * kGjvTy>(ncl, sh, tid);
         if (tid == 0) {
-            a.part[2 * (size_t)blockIdx.x] = d2;
-            a.part[2 * (size_t)blockIdx.x + 1] = n2;
+            a.part[kPart * (size_t)blockIdx.x] = d2;
+            a.part[kPart * (size_t)blockIdx.x + 1] = n2;
+            a.part[kPart * (size_t)blockIdx.x + 2] = c2;
         }
     }
 }
@@ -594,7 +604,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
     uint64_t* ufull = empty + kTmaStages;                      // [2]
     uint64_t* uempty = ufull + 2;                              // [2]
     __shared__ int s_abort, s_issued, s_uissued, s_second;
-    __shared__ double wsum[2][kTmaConsumers / 32];
+    __shared__ double wsum[3][kTmaConsumers / 32];
     const int N = a.N, nx = a.nx, ny = a.ny;
     const int tilesx = (nx + kTmaTW - 1) / kTmaTW;
     const int nunits = tilesx * ((ny + kTmaTH - 1) / kTmaTH) * N * split;
@@ -779,7 +789,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
                 zb[0] += o3.x; zb[1] += o3.y; zb[2] += o3.z; zb[3] += o3.w;
                 if (tid == 0) hcnt[t] = 0;        // ready for the next sweep
             }
-            float dsq = 0.f, nsq = 0.f;
+            float dsq = 0.f, nsq = 0.f, ncl = 0.f;
 #pragma unroll
             for (int p = 0; p < 4; ++p) {
                 const int x = x0 + p;
@@ -791,27 +801,31 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
                     a.uout[i * plane + (size_t)(y + a.pp.oy) * px + x + a.pp.ox] = unew;
                 } else {
                     const float fnew = a.clamp ? fmaxf(unew, 0.f) : unew;
+                    if (a.clamp && unew < 0.f) ncl += 1.f;
                     const float fold = a.fout[i * npx + pix];
                     a.fout[i * npx + pix] = fnew;
                     dsq = fmaf(fnew - fold, fnew - fold, dsq);
                     nsq = fmaf(fnew, fnew, nsq);
                 }
             }
-            if (MODE == 1) {     // relative-change partials of this (tile, phase)
-                const float d = warp_sum(dsq), n = warp_sum(nsq);
+            if (MODE == 1) {     // relative-change and clamp-count partials of this (tile, phase)
+                const float d = warp_sum(dsq), n = warp_sum(nsq), c = warp_sum(ncl);
                 if (lane == 0) {
                     wsum[0][warp] = (double)d;
                     wsum[1][warp] = (double)n;
+                    wsum[2][warp] = (double)c;
                 }
                 consumer_sync();
                 if (tid == 0) {
-                    double d2 = 0.0, n2 = 0.0;
+                    double d2 = 0.0, n2 = 0.0, c2 = 0.0;
                     for (int w = 0; w < kTmaConsumers / 32; ++w) {
                         d2 += wsum[0][w];
                         n2 += wsum[1][w];
+                        c2 += wsum[2][w];
                     }
-                    a.part[2 * (size_t)t] = d2;
-                    a.part[2 * (size_t)t + 1] = n2;
+                    a.part[kPart * (size_t)t] = d2;
+                    a.part[kPart * (size_t)t + 1] = n2;
+                    a.part[kPart * (size_t)t + 2] = c2;
                 }
                 consumer_sync();
             }
@@ -1010,20 +1024,23 @@ cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int win
     if (layout_ok && ws.tm_ok &&
         (fout ? launch_gj_tma<1>(g, a, ws, window, st) : launch_gj_tma<0>(g, a, ws, window, st))) {
         const int nt = gj_tma_tiles(g), nmax = ns > nv ? ns : nv;
-        if (fout && nmax > nt) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nt, 0, 16 * (size_t)(nmax - nt), st);
+        if (fout && nmax > nt)
+            return cudaMemsetAsync(ws.part2 + kPart * (size_t)nt, 0, 8 * kPart * (size_t)(nmax - nt), st);
         return cudaGetLastError();
     }
     if (ws.pp.ox >= ((a.rho + 3) / 4) * 4 + 4 && ws.pp.oy >= a.rho && (ws.pp.px % 4) == 0 &&
         ws.pp.px >= tx64 + 2 * ws.pp.ox && ws.pp.py >= ty16 + 2 * ws.pp.oy &&
         (fout ? launch_gj_vec<1>(a, window, nv, st) : launch_gj_vec<0>(a, window, nv, st))) {
-        if (fout && ns > nv) return cudaMemsetAsync(ws.part2 + 2 * (size_t)nv, 0, 16 * (size_t)(ns - nv), st);
+        if (fout && ns > nv)
+            return cudaMemsetAsync(ws.part2 + kPart * (size_t)nv, 0, 8 * kPart * (size_t)(ns - nv), st);
         return cudaGetLastError();
     }
     if (fout)
         k_gj<1><<<ns, kGjTileX * kGjTileY, 0, st>>>(a);
     else
         k_gj<0><<<ns, kGjTileX * kGjTileY, 0, st>>>(a);
-    if (fout && nv > ns) return cudaMemsetAsync(ws.part2 + 2 * (size_t)ns, 0, 16 * (size_t)(nv - ns), st);
+    if (fout && nv > ns)
+        return cudaMemsetAsync(ws.part2 + kPart * (size_t)ns, 0, 8 * kPart * (size_t)(nv - ns), st);
     return cudaGetLastError();
 }
 
@@ -1045,20 +1062,23 @@ __global__ void __launch_bounds__(256) k_finalize_nogj(const float* __restrict__
     const int x = (tile % tilesx) * kGjTileX + (tid & 31);
     const int y = (tile / tilesx) * kGjTileY + (tid >> 5);
     const size_t npx = (size_t)nx * ny;
-    float fnew = 0.f, dif = 0.f;
+    float fnew = 0.f, dif = 0.f, ncl = 0.f;
     if (x < nx && y < ny) {
         const size_t k = i * npx + (size_t)y * nx + x;
         const float v = gimg[k];
         fnew = clamp ? fmaxf(v, 0.f) : v;
+        ncl = (clamp && v < 0.f) ? 1.f : 0.f;
         dif = fnew - fout[k];
         fout[k] = fnew;
     }
     __shared__ double sh[8];
     const double d2 = block_sum<256>(dif * dif, sh, tid);
     const double n2 = block_sum<256>(fnew * fnew, sh, tid);
+    const double c2 = block_sum<256>(ncl, sh, tid);
     if (tid == 0) {
-        part[2 * (size_t)blockIdx.x] = d2;
-        part[2 * (size_t)blockIdx.x + 1] = n2;
+        part[kPart * (size_t)blockIdx.x] = d2;
+        part[kPart * (size_t)blockIdx.x + 1] = n2;
+        part[kPart * (size_t)blockIdx.x + 2] = c2;
     }
 }
 
@@ -1066,50 +1086,150 @@ cudaError_t launch_finalize_nogj(const tnlm_geometry* g, const Workspace& ws, co
                                  float* fout, int clamp, cudaStream_t st) {
     const int ns = gjs_blocks(g), nv = gjv_blocks(g);
     k_finalize_nogj<<<ns, 256, 0, st>>>(gimg, fout, ws.part2, g->nx, g->ny, g->N, clamp);
-    if (nv > ns) return cudaMemsetAsync(ws.part2 + 2 * (size_t)ns, 0, 16 * (size_t)(nv - ns), st);
+    if (nv > ns) return cudaMemsetAsync(ws.part2 + kPart * (size_t)ns, 0, 8 * kPart * (size_t)(nv - ns), st);
     return cudaGetLastError();
 }
 
-// Per-iteration monitors: relative change and the data term of f^(k-1).
-// 256 threads so that each reads only a few partials (the loads, not the
-// FP64 adds, set the time); a fixed-order tree keeps the sum deterministic.
+// Per-iteration monitors: relative change, data term of f^(k-1), clamped
+// pixels and (monitor on) the TNLM term of Eq. 1.  256 threads so that each
+// reads only a few partials (the loads, not the FP64 adds, set the time); a
+// fixed-order tree keeps the sums deterministic.
 constexpr int kScalThreads = 256;
 __global__ void __launch_bounds__(kScalThreads) k_iter_scalars(const double* part, int nblocks,
+                                                               const double* part3, int n3,
                                                                const double* res0, int N, DevState st,
                                                                int kcap) {
-    __shared__ double sd[kScalThreads], sn[kScalThreads];
-    double d = 0.0, n = 0.0;
+    __shared__ double sd[kScalThreads], sn[kScalThreads], sc[kScalThreads], sj[kScalThreads];
+    double d = 0.0, n = 0.0, c = 0.0, j = 0.0;
     for (int k = threadIdx.x; k < nblocks; k += kScalThreads) {
-        d += part[2 * (size_t)k];
-        n += part[2 * (size_t)k + 1];
+        d += part[kPart * (size_t)k];
+        n += part[kPart * (size_t)k + 1];
+        c += part[kPart * (size_t)k + 2];
     }
+    for (int k = threadIdx.x; k < n3; k += kScalThreads) j += part3[k];
     sd[threadIdx.x] = d;
     sn[threadIdx.x] = n;
+    sc[threadIdx.x] = c;
+    sj[threadIdx.x] = j;
     __syncthreads();
     for (int h = kScalThreads / 2; h > 0; h >>= 1) {
         if (threadIdx.x < h) {
             sd[threadIdx.x] += sd[threadIdx.x + h];
             sn[threadIdx.x] += sn[threadIdx.x + h];
+            sc[threadIdx.x] += sc[threadIdx.x + h];
+            sj[threadIdx.x] += sj[threadIdx.x + h];
         }
         __syncthreads();
     }
-    d = sd[0];
-    n = sn[0];
     if (threadIdx.x == 0) {
+        d = sd[0];
+        n = sn[0];
         double r = 0.0;
         for (int i = 0; i < N; ++i) r += res0[i];
         const int it = *st.iter;
         if (it < kcap) {
             st.hist_rel[it] = n > 0.0 ? sqrt(d / n) : 0.0;
             st.hist_res[it] = r;
+            st.hist_clamp[it] = sc[0];
+            st.hist_tnlm[it] = n3 > 0 ? sj[0] : 0.0;
         }
         *st.iter = it + 1;
     }
 }
 
-cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks,
+cudaError_t launch_iter_scalars(const tnlm_geometry* g, const Workspace& ws, int nblocks, bool monitor,
                                 cudaStream_t st) {
-    k_iter_scalars<<<1, kScalThreads, 0, st>>>(ws.part2, nblocks, ws.st.res0, g->N, ws.st, ws.kcap);
+    k_iter_scalars<<<1, kScalThreads, 0, st>>>(ws.part2, nblocks, ws.part3, monitor ? gjs_blocks(g) : 0,
+                                               ws.st.res0, g->N, ws.st, ws.kcap);
+    return cudaGetLastError();
+}
+
+// TNLM term of Eq. 1 for the monitor: per pixel x of phase i,
+//   J_i(x) = sum_s omega_{i,i+1}(x, x+s) (f_i(x) - f_{i+1}(x+s))^2
+//          + sum_s omega_{i,i-1}(x, x-s) (f_i(x) - f_{i-1}(x-s))^2
+// (Eq. 2 for both neighbours, the weights of this outer iteration: the
+// stored distances and row minima, normalisers formed on the fly as in the
+// sweep), summed per block in FP64; candidates outside the image carry no
+// weight.  f is the unpadded result of the iteration.
+__global__ void __launch_bounds__(kGjTileX * kGjTileY) k_tnlm_energy(GjArgs a, const float* __restrict__ f,
+                                                                    double* __restrict__ part3) {
+    const int N = a.N, nx = a.nx, ny = a.ny;
+    const int tile = blockIdx.x / N, i = blockIdx.x % N;
+    const int tilesx = (nx + kGjTileX - 1) / kGjTileX;
+    const int tid = threadIdx.x;
+    const int x = (tile % tilesx) * kGjTileX + (tid & 31);
+    const int y = (tile / tilesx) * kGjTileY + (tid >> 5);
+    const bool in = x < nx && y < ny;
+    const size_t npx = (size_t)nx * ny;
+    const int ip = (i + N - 1) % N, inx = (i + 1) % N;
+    float jt = 0.f;
+    if (in) {
+        const int rho = a.rho, W = a.W, px = a.pp.px;
+        const size_t plane = a.pp.plane, W2 = (size_t)W * W;
+        const float k2 = a.k2;
+        const size_t pix = (size_t)y * nx + x;
+        const float mfk = a.mins[i * npx + pix] * k2;
+        const float mbk = a.mins[(N + i) * npx + pix] * k2;
+        const float fi = f[i * npx + pix];
+        const float* fn = f + inx * npx;
+        const float* fp = f + ip * npx;
+        const size_t cpos = (size_t)(y + a.pp.oy) * px + x + a.pp.ox;
+        const float* dn = a.D + (size_t)i * W2 * plane + cpos;
+        const float* dp = a.D + (size_t)ip * W2 * plane + cpos + (size_t)rho * px + rho;
+        float jf = 0.f, zf = 0.f, jb = 0.f, zb = 0.f;
+        for (int sy = 0; sy < W; ++sy) {
+            const int yn = y + sy - rho, yp = y - sy + rho;
+            const float* dnr = dn + (size_t)sy * W * plane;
+            const float* dpr = dp + (size_t)sy * W * plane - (size_t)sy * px;
+            for (int sx = 0; sx < W; ++sx) {
+                const int xn = x + sx - rho, xp = x - sx + rho;
+                const float ef = ex2_approx(fmaf(-__ldg(dnr + (size_t)sx * plane), k2, mfk));
+                const float eb = ex2_approx(fmaf(-__ldg(dpr + (size_t)sx * plane - sx), k2, mbk));
+                zf += ef;
+                zb += eb;
+                if ((unsigned)xn < (unsigned)nx && (unsigned)yn < (unsigned)ny) {
+                    const float dv = fi - fn[(size_t)yn * nx + xn];
+                    jf = fmaf(ef, dv * dv, jf);
+                }
+                if ((unsigned)xp < (unsigned)nx && (unsigned)yp < (unsigned)ny) {
+                    const float dv = fi - fp[(size_t)yp * nx + xp];
+                    jb = fmaf(eb, dv * dv, jb);
+                }
+            }
+        }
+        jt = jf / zf + jb / zb;
+    }
+    __shared__ double sh[kGjTileX * kGjTileY / 32];
+    const double tot = block_sum<kGjTileX * kGjTileY>(jt, sh, tid);
+    if (tid == 0) part3[blockIdx.x] = tot;
+}
+
+int tnlm_energy_blocks(const tnlm_geometry* g) { return gjs_blocks(g); }
+
+cudaError_t launch_tnlm_energy(const tnlm_geometry* g, const Workspace& ws, int window, double h,
+                               const float* f, cudaStream_t st) {
+    GjArgs a = gj_args(g, ws, window, h, 0.0);
+    k_tnlm_energy<<<gjs_blocks(g), kGjTileX * kGjTileY, 0, st>>>(a, f, ws.part3);
+    return cudaGetLastError();
+}
+
+// Data term of the final image (monitor): the FP64 sum of the projector's
+// per-(phase, view, chunk) partials of ||sqrt(w)(y - P f)||^2.
+__global__ void __launch_bounds__(kScalThreads) k_sum_partials(const double* part, int n, double* out) {
+    __shared__ double sh[kScalThreads];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += kScalThreads) s += part[k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = kScalThreads / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+cudaError_t launch_sum_partials(const double* part, int n, double* out, cudaStream_t st) {
+    k_sum_partials<<<1, kScalThreads, 0, st>>>(part, n, out);
     return cudaGetLastError();
 }
 

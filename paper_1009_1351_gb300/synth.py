@@ -75,6 +75,7 @@ class Params:
     data_step: int = 0        # 0 = CGLS, 1 = gradient step (Eq. 4)
     clamp: int = 1            # positivity truncation after each outer iteration
     precision: int = 0        # 0: FP32; 1: split-FP16 tensor-core patch cross terms
+    monitor: int = 0          # 1: FP64 TNLM term / objective of Eq. 1 every iteration
 
 
 @dataclasses.dataclass(frozen=True)
