@@ -40,20 +40,27 @@ def _deps() -> List[str]:
 
 def flags() -> List[str]:
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
-                   "-I", CSRC, "--expt-relaxed-constexpr"]
+                   "-I", CSRC, "--expt-relaxed-constexpr"] + _defines()
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    os.makedirs(OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB):
-        t = os.path.getmtime(LIB)
+def _defines() -> List[str]:
+    """Extra -D flags (TNLM_DEFINES="A=1 B=2"), for builds that try other
+    compile-time launch constants; none by default."""
+    return ["-D" + d for d in os.environ.get("TNLM_DEFINES", "").split()]
+
+
+def build(force: bool = False, verbose: bool = False, out_dir: str = OUT_DIR) -> str:
+    lib = os.path.join(out_dir, "libtnlm.so")
+    os.makedirs(out_dir, exist_ok=True)
+    if not force and os.path.exists(lib):
+        t = os.path.getmtime(lib)
         if all(os.path.getmtime(p) <= t for p in _deps()):
-            return LIB
+            return lib
     nvcc = _nvcc()
     objs = []
 
     def one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src)[:-3] + ".o")
         cmd = [nvcc] + flags() + ["-c", src, "-o", obj]
         if verbose:
             cmd += ["-Xptxas", "-v"]
@@ -67,13 +74,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             objs.append(obj)
             if verbose and log:
                 print(log)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -168,13 +168,17 @@ __device__ __forceinline__ Cut line_cut(float kk, float am, float ik, float kf, 
 // units); am = alpha + min(kk, 0) is the lower end of the ray's span inside
 // line 0.  With v0, v1 the values at the lower line index and the next, the
 // pair holds (v0 - v1, v1) and the ray accumulates frac * (v0 - v1) + v1.
+#ifndef TNLM_PROJ_UNROLL
+#define TNLM_PROJ_UNROLL 4
+#endif
+constexpr int kProjUnroll = TNLM_PROJ_UNROLL;   // lines per unrolled step of a ray's march
 __device__ __forceinline__ float march(const float2* __restrict__ base, int pitch, int nacross,
                                        float kk, float am, float ik, int lo, int hi, bool on) {
     float acc = 0.f;
     float kf = (float)lo;
     int koff = lo * pitch;
     const float na = (float)nacross;
-#pragma unroll 4
+#pragma unroll kProjUnroll
     for (int k = lo; k <= hi; ++k) {
         const Cut c = line_cut(kk, am, ik, kf, na);
         if (on) {

@@ -542,7 +542,10 @@ constexpr int kTmaBW = kTmaTW + 4;
 constexpr int kTmaConsumers = 256;
 constexpr int kTmaThreads = kTmaConsumers + 32;
 constexpr int kTmaStageFloats = kTmaTH * (kTmaTW + kTmaBW);   // 2112 floats = 66 x 128 B
-constexpr int kTmaStages = 6;
+#ifndef TNLM_GJ_STAGES
+#define TNLM_GJ_STAGES 6
+#endif
+constexpr int kTmaStages = TNLM_GJ_STAGES;
 constexpr int kTmaUBufs = 1;      // neighbour-iterate tile buffers (2 lets a multi-tile CTA load the next tile early)
 // neighbour-phase tile: the 64 x 16 pixels widened by 8 columns and 7 rows
 // on each side (every window up to 15 x 15), loaded once per block
