@@ -82,12 +82,14 @@ def phantom_gpu(torch, c: synth.Case, offset, dev, ss: int = 4):
 class PairMaker:
     """Makes (per-phase FBP, all-views FBP, TNLM target, truth) on the GPU."""
 
-    def __init__(self, torch, tn, slots: int = 16, k_outer: int = 50, tol: float = 0.0):
+    def __init__(self, torch, tn, slots: int = 16, k_outer: int = 50, tol: float = 0.0,
+                 scenarios=SCENARIOS):
         self.torch, self.tn, self.k, self.tol = torch, tn, k_outer, tol
         self.dev = torch.device("cuda")
-        self.cases = {s: synth.case(s) for s in SCENARIOS}
+        self.scenarios = tuple(scenarios)
+        self.cases = {s: synth.case(s) for s in self.scenarios}
         self.geos = {s: [tn.tnlm_create_geometry(self.cases[s].geom) for _ in range(slots)]
-                     for s in SCENARIOS}
+                     for s in self.scenarios}
         self.slots = slots
 
     def make(self, seeds: List[int], keep_all: bool = True) -> Dict[str, "object"]:
@@ -95,7 +97,7 @@ class PairMaker:
         out = {"inp": [], "init": [], "target": [], "truth": [], "scenario": [], "seed": []}
         by_sc: Dict[str, List[int]] = {}
         for sd in seeds:
-            by_sc.setdefault(SCENARIOS[sd % 3], []).append(sd)
+            by_sc.setdefault(self.scenarios[sd % len(self.scenarios)], []).append(sd)
         for sc, lst in by_sc.items():
             c = self.cases[sc]
             p = synth.Params(**{**c.params.__dict__, "k_outer": self.k})
@@ -167,6 +169,7 @@ def evaluate(torch, tn, net, maker: PairMaker, data, tol: float, kmax: int):
                 o = torch.empty_like(x)
                 net.forward(x, o)
                 f = torch.clamp(o[0] / SCALE, min=0.0).contiguous()
+            data.setdefault("start", {}).setdefault(i, {})[mode] = f.clone()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
             e0.record()
@@ -174,6 +177,7 @@ def evaluate(torch, tn, net, maker: PairMaker, data, tol: float, kmax: int):
             e1.record()
             e1.synchronize()
             res[mode] = (f, rep["iterations"], e0.elapsed_time(e1))
+            data.setdefault("result", {}).setdefault(i, {})[mode] = (f, rep["iterations"])
         data.setdefault("cold_result", {})[i] = res["cold"][0]
         fc, fw = res["cold"][0].double(), res["warm"][0].double()
         t = truth.double()
@@ -208,13 +212,13 @@ def evaluate_batched(torch, tn, net, maker: PairMaker, data, tol: float, kmax: i
     gains."""
     import types
     n = len(data["seed"])
-    pool: Dict[str, List[object]] = {s: [] for s in SCENARIOS}
+    pool: Dict[str, List[object]] = {s: [] for s in maker.scenarios}
     tot = {"batched_cold_ms": 0.0, "batched_warm_ms": 0.0}
     iters = {"batched_cold": [], "batched_warm": []}
     err_truth, vs_cold = [], []
     for c0 in range(0, n, chunk):
         idx = list(range(c0, min(n, c0 + chunk)))
-        used = {s: 0 for s in SCENARIOS}
+        used = {s: 0 for s in maker.scenarios}
         geos, ps = [], []
         for i in idx:
             sc = data["scenario"][i]

@@ -82,3 +82,29 @@ def test_bf16_rounding_is_nearest_even(un):
     assert r[2] == 1.0 + 2 ** -6           # halfway, ties to even (odd lsb rounds up)
     assert r[3] == -3.140625
     assert abs(r[4] - 1e-3) <= 2 ** -9 * 1e-3
+
+
+@pytest.mark.parametrize("cin,base,L,H,W,B", [(3, 4, 2, 16, 24, 2), (10, 8, 3, 32, 32, 2)])
+def test_bf16_storage_stays_within_the_roundoff_bound(cin, base, L, H, W, B):
+    """The oracle rounding at the GPU's points differs from the plain FP64
+    network by less than the first-order bound the GPU tests use: u = 2^-8
+    per rounding point, 2 + 2 n3 points on the correction, 1 + 3 n3 on every
+    parameter gradient (n3 = number of 3x3 layers)."""
+    from oracle import unet_oracle as un
+    rng = np.random.default_rng(100 + L)
+    p = un.init_params(cin, cin, base, L, 100 + L)
+    p = [((w + 0.05 * rng.standard_normal(w.shape)).astype(np.float32).astype(np.float64),
+          (b + 0.05 * rng.standard_normal(b.shape)).astype(np.float32).astype(np.float64)) for w, b in p]
+    x = np.random.default_rng(7).random((B, cin, H, W)).astype(np.float32).astype(np.float64)
+    t = x + 0.1 * np.random.default_rng(8).standard_normal(x.shape)
+    n3 = 2 * L + 2 * (L - 1)
+    u = 2.0 ** -8
+    o1, _ = un.forward(p, x, L, bf16_storage=True)
+    o0, _ = un.forward(p, x, L, bf16_storage=False)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    assert rel(o1 - un.bf16(x), o0 - x) <= u * (2 + 2 * n3)
+    _, g1, _ = un.loss_and_grads(p, x, t, L, bf16_storage=True)
+    _, g0, _ = un.loss_and_grads(p, x, t, L, bf16_storage=False)
+    for (w1, b1), (w0, b0) in zip(g1, g0):
+        assert rel(w1, w0) <= u * (1 + 3 * n3)
+        assert rel(b1, b0) <= u * (1 + 3 * n3)
