@@ -230,19 +230,23 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* geom, const tnlm_params* param
  * arithmetic is laid out on the device).  Runs one outer iteration of the
  * algorithm box from d_f0 on a scratch copy (d_f0 is not modified), then
  * times the backprojection with 1..4 view groups (CTAs) per 32 x 32 tile and
- * the Gauss-Jacobi sweep with 1..3 pixel tiles per CTA, and keeps the
- * fastest choice in the handle (used by every later call on it).  Results
- * are cached per device and shape (nx, ny, N, V, B, window, patch): a second
- * handle of the same shape is tuned without timing.  The choice changes
- * launch shapes only: the sweep's tiling leaves results bitwise unchanged;
- * the number of view groups changes the order in which the FP32
- * backprojection sums its views, so results may differ in the last bits
- * (each choice is deterministic).  Synchronises the stream; allocates one image-sized scratch
- * buffer for the duration of the call.  bp_groups / gj_tiles (may be NULL)
- * receive the choice.  Errors: as tnlm_reconstruct. */
+ * the Gauss-Jacobi sweep with 1..3 pixel tiles per CTA under two window
+ * schedules (each work unit takes the whole W x W window of its tile, or
+ * the window rows in two halves as separate units whose partial sums the
+ * second to finish adds), and keeps the fastest choice in the handle (used
+ * by every later call on it).  Results are cached per device and shape
+ * (nx, ny, N, V, B, window, patch): a second handle of the same shape is
+ * tuned without timing.  The choice changes launch shapes only: the tiles
+ * per CTA leave results bitwise unchanged; the number of view groups and
+ * the window schedule change the order of FP32 sums (results may differ in
+ * the last bits; each choice is deterministic).  Synchronises the stream;
+ * allocates one image-sized scratch buffer for the duration of the call.
+ * bp_groups / gj_tiles / gj_split (may be NULL) receive the choice (gj_split
+ * 1: whole window, 2: two halves, 0: no sweep tuned).  Errors: as
+ * tnlm_reconstruct. */
 tnlm_status tnlm_autotune(tnlm_geometry* geom, const tnlm_params* params, const float* d_y,
                           const float* d_winv, const float* d_f0, int* bp_groups, int* gj_tiles,
-                          void* stream);
+                          int* gj_split, void* stream);
 
 /* Batched reconstruction of many independent slices (each its own handle,
  * sizes, view counts and parameters may differ; all on one device).  Each

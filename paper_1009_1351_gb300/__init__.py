@@ -120,7 +120,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_reconstruct.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp,
                                      ctypes.POINTER(ReportC), vp]
     lib.tnlm_autotune.argtypes = [vp, ctypes.POINTER(ParamsC), vp, vp, vp, ctypes.POINTER(ctypes.c_int),
-                                  ctypes.POINTER(ctypes.c_int), vp]
+                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp]
     lib.tnlm_reconstruct_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(ParamsC), ctypes.c_int,
                                            ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
                                            ctypes.POINTER(ReportC), ctypes.c_int, vp]
@@ -302,12 +302,13 @@ def tnlm_reconstruct(geom: Geometry, params, y, winv, f, report: bool = True,
 
 def tnlm_autotune(geom: Geometry, params, y, winv, f0, stream=None) -> Dict[str, int]:
     """Measure and keep the fastest launch shapes for this handle (f0 is not
-    modified).  Returns {"bp_groups": G, "gj_tiles": T}."""
+    modified).  Returns {"bp_groups": G, "gj_tiles": T, "gj_split": S}."""
     pc = params_c(params)
-    bg, gt = ctypes.c_int(0), ctypes.c_int(0)
+    bg, gt, gs = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
     _check(load_library().tnlm_autotune(geom.handle, ctypes.byref(pc), _ptr(y), _ptr(winv), _ptr(f0),
-                                        ctypes.byref(bg), ctypes.byref(gt), _stream(stream)))
-    return {"bp_groups": bg.value, "gj_tiles": gt.value}
+                                        ctypes.byref(bg), ctypes.byref(gt), ctypes.byref(gs),
+                                        _stream(stream)))
+    return {"bp_groups": bg.value, "gj_tiles": gt.value, "gj_split": gs.value}
 
 
 def tnlm_reconstruct_batch(geoms, params, ys, winvs, fs, autotune: bool = True,

@@ -426,21 +426,25 @@ tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_
 // ---------------------------------------------------------------------------
 // Autotuner: measures the launch choices of the two kernels whose best shape
 // depends on the device and the workload -- the number of view groups (CTAs)
-// per backprojection tile and the number of tiles per CTA of the TMA sweep --
-// and keeps the fastest.  Results are cached per device and shape.
+// per backprojection tile, and for the TMA sweep the number of pixel tiles
+// per CTA together with the window schedule (the whole window per work unit,
+// or its rows in two halves as separate units) -- and keeps the fastest.
+// Results are cached per device and shape.
 // ---------------------------------------------------------------------------
 std::atomic<unsigned long long> g_uid{1};
 std::mutex g_tune_mu;
-std::map<std::array<int, 8>, std::array<int, 2>> g_tune_cache;
+std::map<std::array<int, 8>, std::array<int, 3>> g_tune_cache;
 
 std::array<int, 8> tune_key(const tnlm_geometry* g, const tnlm_params* p) {
     return {g->device, g->nx, g->ny, g->N, g->V, g->B, p->window, p->patch};
 }
 
-void set_tuning(tnlm_geometry* g, int bp_groups, int gj_tpb) {
-    if (g->tune_bp_groups != bp_groups || g->tune_gj_tpb != gj_tpb || g->tune_gen == 0) {
+void set_tuning(tnlm_geometry* g, int bp_groups, int gj_tpb, int gj_split) {
+    if (g->tune_bp_groups != bp_groups || g->tune_gj_tpb != gj_tpb || g->tune_gj_split != gj_split ||
+        g->tune_gen == 0) {
         g->tune_bp_groups = bp_groups;
         g->tune_gj_tpb = gj_tpb;
+        g->tune_gj_split = gj_split;
         g->tune_gen++;
     }
 }
@@ -477,7 +481,7 @@ tnlm_status autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y, c
         std::lock_guard<std::mutex> lock(g_tune_mu);
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
-            set_tuning(g, it->second[0], it->second[1]);
+            set_tuning(g, it->second[0], it->second[1], it->second[2]);
             return TNLM_OK;
         }
     }
@@ -501,7 +505,7 @@ tnlm_status autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y, c
         LK(TNLM_KCLASS_PREP, launch_sqrt(d_winv, ws.sw, nsg, ws.st.err, st), "sqrt");
         tnlm_status r = outer_iteration(g, p, d_y, f, st);
         if (r != TNLM_OK) return r;
-        int best_g = 1, best_t = 1;
+        int best_g = 1, best_t = 1, best_s = 1;
         float tb = INFINITY;
         for (int G = 1; G <= bp_max_groups(g); ++G) {
             g->tune_bp_groups = G;
@@ -512,20 +516,23 @@ tnlm_status autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y, c
         }
         if (p->m2 > 0) {
             float tg = INFINITY;
-            for (int t = 1; t <= 3; ++t) {
-                g->tune_gj_tpb = t;
-                float ms = 0.f;
-                r = time_calls(st, 3, [&]() {
-                    return launch_gj_sweep(g, ws, p->window, p->h, p->mu_hat, ws.u, ws.U0, ws.U1, nullptr,
-                                           p->clamp, st);
-                }, &ms);
-                if (r != TNLM_OK) return r;
-                if (ms < tg) { tg = ms; best_t = t; }
-            }
+            for (int sp = 1; sp <= 2; ++sp)
+                for (int t = 1; t <= 3; ++t) {
+                    g->tune_gj_tpb = t;
+                    g->tune_gj_split = sp;
+                    float ms = 0.f;
+                    r = time_calls(st, 3, [&]() {
+                        return launch_gj_sweep(g, ws, p->window, p->h, p->mu_hat, ws.u, ws.U0, ws.U1, nullptr,
+                                               p->clamp, st);
+                    }, &ms);
+                    if (r != TNLM_OK) return r;
+                    if (ms < tg) { tg = ms; best_t = t; best_s = sp; }
+                }
         }
         g->tune_bp_groups = 0;
         g->tune_gj_tpb = 0;
-        set_tuning(g, best_g, best_t);
+        g->tune_gj_split = 0;
+        set_tuning(g, best_g, best_t, p->m2 > 0 ? best_s : 0);
         CK(cudaMemsetAsync(ws.st.iter, 0, sizeof(int), st), "reset");
         CK(cudaMemsetAsync(ws.st.err, 0, sizeof(int), st), "reset");
         CK(cudaStreamSynchronize(st), "sync");
@@ -539,10 +546,11 @@ tnlm_status autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y, c
     if (s != TNLM_OK) {
         g->tune_bp_groups = 0;
         g->tune_gj_tpb = 0;
+        g->tune_gj_split = 0;
         return s;
     }
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune_cache[key] = {g->tune_bp_groups, g->tune_gj_tpb};
+    g_tune_cache[key] = {g->tune_bp_groups, g->tune_gj_tpb, g->tune_gj_split};
     return TNLM_OK;
 }
 
@@ -1275,7 +1283,7 @@ tnlm_status tnlm_reconstruct(const tnlm_geometry* gc, const tnlm_params* p, cons
 
 tnlm_status tnlm_autotune(tnlm_geometry* g, const tnlm_params* p, const float* d_y,
                           const float* d_winv, const float* d_f0, int* bp_groups, int* gj_tiles,
-                          void* stream) {
+                          int* gj_split, void* stream) {
     g_err[0] = 0;
     if (check_geom_handle(g) != TNLM_OK) return TNLM_ERR_INVALID_ARG;
     tnlm_status s = check_params(p);
@@ -1289,6 +1297,7 @@ tnlm_status tnlm_autotune(tnlm_geometry* g, const tnlm_params* p, const float* d
     if (s != TNLM_OK) return s;
     if (bp_groups) *bp_groups = g->tune_bp_groups;
     if (gj_tiles) *gj_tiles = g->tune_gj_tpb;
+    if (gj_split) *gj_split = g->tune_gj_split;
     return TNLM_OK;
 }
 

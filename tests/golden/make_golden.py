@@ -19,6 +19,14 @@ residual after every iteration and 8192 pixel values at seeded positions
 over the whole image.  At 8 host threads one file takes 30-60 minutes.
 
     python tests/golden/make_golden.py large_a large_b
+
+batch<i>_k50.txt: the four slices sampled from the 64-slice batched
+workload (the first of each side length 256 / 384 / 512 and the first other
+60-view slice; d = 5, W = 11, h = 0.01, mu_hat = 0.5, M1 = 3, M2 = 5), the
+full K = 50 outer iterations from the constant start 0.01: histories and
+4096 pixel values at seeded positions.
+
+    python tests/golden/make_golden.py batch
 """
 import os
 import sys
@@ -116,6 +124,57 @@ def read_large(name):
     return read_tiny_k3(large_path(name))
 
 
+BATCH_K = 50
+BATCH_SAMPLES = 4096
+BATCH_SEED = 1618
+
+
+def batch_pick(items):
+    """Indices of the four sampled slices of the batched workload: the first
+    slice of each side length, then the first remaining 60-view slice."""
+    pick, seen = [], set()
+    for i, (c, _) in enumerate(items):
+        if c.geom.nx not in seen:
+            seen.add(c.geom.nx)
+            pick.append(i)
+    pick.append(next(i for i, (c, _) in enumerate(items) if c.geom.n_views == 60 and i not in pick))
+    return pick
+
+
+def batch_path(i):
+    return os.path.join(HERE, f"batch{i:02d}_k{BATCH_K}.txt")
+
+
+def write_batch(i):
+    """Slice i of the 64-slice batched workload, K = 50 outer iterations from
+    the constant start 0.01 (the oracle has no mixed precision: FP64 throughout)."""
+    import oracle
+    from paper_1009_1351_gb300 import synth
+    c, off = synth.batch_cases(64)[i]
+    assert c.params.k_outer == BATCH_K
+    d = synth.make_inputs(c, off)
+    G = oracle.Geom(c.geom)
+    f0 = np.full((c.geom.n_phases, c.geom.ny, c.geom.nx), 0.01, np.float32)
+    f, rel, res = oracle.reconstruct(G, d["y"].astype(np.float32), d["w"].astype(np.float32), f0, c.params)
+    pos = large_positions(f.shape, BATCH_SAMPLES, BATCH_SEED)
+    with open(batch_path(i), "w") as fh:
+        fh.write(f"# TNLM algorithm box, slice {i} of the batched workload ({c.geom.nx}^2, "
+                 f"{c.geom.n_views} views), K = {BATCH_K} from f0 = 0.01 (FP64 oracle).\n")
+        fh.write("# Written by tests/golden/make_golden.py; see its docstring for the workload.\n")
+        fh.write("# iter <k> <relative change> <data residual>\n")
+        fh.write("# pixel <phase> <row> <column> <value>\n")
+        for k in range(len(rel)):
+            fh.write(f"iter {k + 1} {float(rel[k])!r} {float(res[k])!r}\n")
+        for ph, y, x in pos:
+            fh.write(f"pixel {ph} {y} {x} {float(f[ph, y, x])!r}\n")
+
+
+def read_batch(i):
+    if not os.path.exists(batch_path(i)):
+        return None
+    return read_tiny_k3(batch_path(i))
+
+
 def read_tiny_k3(path=os.path.join(HERE, "tiny_k3.txt")):
     iters, pix = [], []
     for line in open(path):
@@ -137,6 +196,11 @@ if __name__ == "__main__":
         if nm == "tiny":
             write_tiny_k3()
             print("wrote", os.path.join(HERE, "tiny_k3.txt"))
+        elif nm == "batch":
+            from paper_1009_1351_gb300 import synth
+            for i in batch_pick(synth.batch_cases(64)):
+                write_batch(i)
+                print("wrote", batch_path(i), flush=True)
         else:
             write_large(nm)
             print("wrote", large_path(nm))

@@ -177,7 +177,7 @@ def test_autotune_choices_leave_results_unchanged(tn):
     keep = f0.clone()
     choice = tn.tnlm_autotune(g, p, y, w, f0)
     assert torch.equal(f0, keep)                       # the start image is untouched
-    assert 1 <= choice["bp_groups"] <= 4 and 1 <= choice["gj_tiles"] <= 3
+    assert 1 <= choice["bp_groups"] <= 4 and 1 <= choice["gj_tiles"] <= 3 and choice["gj_split"] in (1, 2)
     f_tuned = f0.clone()
     tn.tnlm_reconstruct(g, p, y, w, f_tuned)
     a, b = f_tuned.double(), f_default.double()
@@ -207,13 +207,9 @@ def test_batch_workload_sampled_slices_match_oracle(tn, oracle_mod):
     length and a 60-view one), mixed-precision patch distances, batched and
     autotuned, after K = 2 outer iterations: relative L2 <= 1e-3 against the
     FP64 oracle (the workload's accuracy bound)."""
+    from tests.golden import make_golden
     items = synth.batch_cases(64)
-    pick, seen = [], set()
-    for i, (c, _) in enumerate(items):
-        if c.geom.nx not in seen:
-            seen.add(c.geom.nx)
-            pick.append(i)
-    pick.append(next(i for i, (c, _) in enumerate(items) if c.geom.n_views == 60 and i not in pick))
+    pick = make_golden.batch_pick(items)
     geoms, ps, ys, ws, fs, ins = [], [], [], [], [], []
     for i in pick:
         c, off = items[i]
@@ -234,6 +230,41 @@ def test_batch_workload_sampled_slices_match_oracle(tn, oracle_mod):
         got = f.double().cpu().numpy()
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= 1e-3, (c.name, err)
+
+
+def test_batch_workload_sampled_slices_at_full_k_match_the_stored_oracle(tn):
+    """The same four sampled slices at the workload's own K = 50, run the way
+    the batched workload runs (mixed-precision patch distances, autotuned,
+    one batched launch), against the FP64 oracle's values stored in
+    tests/golden/batch<i>_k50.txt (written by tests/golden/make_golden.py
+    from the oracle alone): 4096 seeded pixels per slice within relative L2
+    1e-3, the workload's accuracy bound."""
+    from tests.golden import make_golden
+    items = synth.batch_cases(64)
+    pick = make_golden.batch_pick(items)
+    golds = [make_golden.read_batch(i) for i in pick]
+    if any(gd is None for gd in golds):
+        pytest.skip("tests/golden/batch*_k50.txt not written")
+    geoms, ps, ys, ws, fs = [], [], [], [], []
+    for i in pick:
+        c, off = items[i]
+        assert c.params.k_outer == make_golden.BATCH_K and c.params.precision == tn.PREC_MIXED
+        d = synth.make_inputs(c, off)
+        geoms.append(tn.tnlm_create_geometry(c.geom))
+        ps.append(c.params)
+        ys.append(dev(d["y"]))
+        ws.append(dev(d["w"]))
+        fs.append(dev(np.full((c.geom.n_phases, c.geom.ny, c.geom.nx), 0.01)))
+    reps = tn.tnlm_reconstruct_batch(geoms, ps, ys, ws, fs, autotune=True)
+    torch.cuda.synchronize()
+    for i, f, gd, r in zip(pick, fs, golds, reps):
+        assert r["iterations"] == make_golden.BATCH_K
+        pix = gd[1]
+        got_f = f.double().cpu().numpy()
+        got = np.array([got_f[a, y, x] for a, y, x, _ in pix])
+        want = np.array([v for _, _, _, v in pix])
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        assert err <= 1e-3, (i, err)
 
 
 def test_batch_edge_rules_zero_iterations_and_first_check(tn):
