@@ -90,7 +90,7 @@ typedef struct {
     int precision;   /* TNLM_PREC_FP32: every step in FP32 (FP64 reductions);
                         TNLM_PREC_MIXED: the patch-distance cross terms of Eq. 8 as
                         split-FP16 tensor-core products with FP32 accumulation
-                        (patch <= 5, window <= 11), all else as FP32 */
+                        (patch <= 7, window 3..15), all else as FP32 */
     int monitor;     /* 1: every outer iteration also reduces, in FP64, the TNLM term
                         of Eq. 1 (J of Eq. 2 toward both neighbours, with that
                         iteration's weights, at the iteration's result), and the call

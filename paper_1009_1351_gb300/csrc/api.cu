@@ -140,7 +140,7 @@ tnlm_status check_params(const tnlm_params* p) {
     if (p->precision != TNLM_PREC_FP32 && p->precision != TNLM_PREC_MIXED)
         return fail(TNLM_ERR_INVALID_ARG, "precision must be TNLM_PREC_FP32 or TNLM_PREC_MIXED");
     if (p->precision == TNLM_PREC_MIXED && !weights_tc_supported(p->patch, p->window))
-        return fail(TNLM_ERR_INVALID_ARG, "mixed precision supports patch <= 5 and window in [3, 11]");
+        return fail(TNLM_ERR_INVALID_ARG, "mixed precision supports patch <= 7 and window in [3, 15]");
     if (p->monitor != 0 && p->monitor != 1) return fail(TNLM_ERR_INVALID_ARG, "monitor must be 0 or 1");
     return TNLM_OK;
 }

@@ -5,7 +5,9 @@ cross term as split-FP16 tcgen05 products (FP32 accumulation) and the
 self-norms in FP32.  Against the FP64 oracle the distances must agree to an
 absolute 1e-7 (the patch energies are ~1e-2, h^2 ~ 1e-4), the normalised
 weights to 1e-4, and a full reconstruction to the mixed-precision bound of
-relative L2 <= 1e-3 (it lands far inside it).
+relative L2 <= 1e-3 (it lands far inside it), also on the 512 x 512 slice
+with 7 x 7 patches and a 15 x 15 window, whose 660 candidates per tile take
+two passes through the tensor-memory accumulator.
 """
 import numpy as np
 import pytest
@@ -51,7 +53,9 @@ def gpu_weights(tn, geo, g, d, W, h, precision):
 
 
 @pytest.mark.parametrize("shape,d,W", [((3, 21, 35), 3, 5), ((3, 40, 70), 5, 11),
-                                       ((4, 17, 33), 1, 3), ((3, 29, 50), 5, 7)])
+                                       ((4, 17, 33), 1, 3), ((3, 29, 50), 5, 7),
+                                       ((3, 37, 45), 7, 15), ((3, 40, 52), 7, 11),
+                                       ((3, 33, 40), 5, 15), ((3, 30, 41), 7, 5)])
 def test_mixed_distances_match_oracle(tn, oracle_mod, shape, d, W):
     N, ny, nx = shape
     geom = synth.Geometry(nx=nx, ny=ny, pixel_mm=1.0, n_phases=N, n_views=4, n_bins=16,
@@ -77,7 +81,7 @@ def test_mixed_distances_match_oracle(tn, oracle_mod, shape, d, W):
     np.testing.assert_allclose(norm[3], norm32[3], rtol=1e-3)
 
 
-@pytest.mark.parametrize("name,k", [("tiny", 20), ("mid_c", 3)])
+@pytest.mark.parametrize("name,k", [("tiny", 20), ("mid_c", 3), ("large_b", 3)])
 def test_mixed_reconstruction_matches_oracle(tn, oracle_mod, name, k):
     c = synth.case(name)
     d = synth.make_inputs(c)
@@ -101,7 +105,7 @@ def test_mixed_reconstruction_matches_oracle(tn, oracle_mod, name, k):
 def test_mixed_rejects_unsupported_shapes(tn):
     c = synth.case("tiny")
     geo = tn.tnlm_create_geometry(c.geom)
-    p = synth.Params(patch=7, window=5, h=0.01, precision=tn.PREC_MIXED)
+    p = synth.Params(patch=9, window=5, h=0.01, precision=tn.PREC_MIXED)
     g = torch.zeros((10, 64, 64), device="cuda")
     dist = torch.zeros((10, 25, 64, 64), device="cuda")
     norm = torch.zeros((4, 10, 64, 64), device="cuda")
