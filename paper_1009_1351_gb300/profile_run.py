@@ -1,9 +1,11 @@
 """Run one named workload through the library, for profilers (ncu) and timing.
 
     python -m paper_1009_1351_gb300.profile_run --case mid_a --k 1 [--m1 3 --m2 5] [--ops 10] [--mixed]
+    python -m paper_1009_1351_gb300.profile_run --case large_a,large_b,large_c,large_d --k 2 --fbp
 
-Builds the seeded inputs of the workload, runs tnlm_reconstruct with K outer
-iterations from the constant start image, then --ops projections and --ops
+Builds the seeded inputs of each named workload, runs tnlm_reconstruct with
+K outer iterations from the constant start image (or, with --fbp, from the
+FBP of all views, as the benchmark does), then --ops projections and --ops
 backprojections of a random image, and prints the CUDA-event time of each
 part.  Everything runs in the library's kernels.
 """
@@ -26,8 +28,14 @@ def main() -> None:
     ap.add_argument("--ops", type=int, default=0)
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--mixed", action="store_true", help="tensor-core patch distances")
+    ap.add_argument("--fbp", action="store_true", help="start from the FBP of all views")
     args = ap.parse_args()
-    c = synth.case(args.case)
+    for name in args.case.split(","):
+        run_case(name, args)
+
+
+def run_case(name: str, args) -> None:
+    c = synth.case(name)
     d = synth.make_inputs(c)
     over = {"k_outer": args.k}
     if args.m1 is not None:
@@ -41,6 +49,8 @@ def main() -> None:
     dv = lambda a: torch.tensor(a, dtype=torch.float32, device="cuda")
     y, w = dv(d["y"]), dv(d["w"])
     f0 = torch.full(geo.img_shape, 0.01, device="cuda")
+    if args.fbp:
+        tn.tnlm_fbp(geo, y, f0)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     for r in range(args.repeat):
         f = f0.clone()
@@ -49,7 +59,7 @@ def main() -> None:
         tn.tnlm_reconstruct(geo, p, y, w, f, report=False)
         e1.record()
         torch.cuda.synchronize()
-        print(f"{args.case} reconstruct K={args.k}: {e0.elapsed_time(e1):.3f} ms")
+        print(f"{name} reconstruct K={args.k}: {e0.elapsed_time(e1):.3f} ms")
     if args.ops:
         img = dv(synth.random_images(geo.img_shape, 1))
         sino = torch.zeros(geo.sino_shape, device="cuda")
