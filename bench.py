@@ -187,11 +187,26 @@ def measured_traffic(cls: str, case_names):
     return float(np.mean(vals))
 
 
-def alu_peak_tops():
-    """FP32-pipe peak: 152 SMs x 128 lanes x one operation per lane and clock
-    x max SM clock (an FMA counts as one operation, as in the per-nnz count)."""
-    mhz = _peaks().get("sm_max_mhz", 2070.0)
-    return 152 * 128 * mhz * 1e6 / 1e12
+_ALU_PEAK = {}
+
+
+def alu_peak_tops(device: int = 0):
+    """FP32-pipe peak in T lane operations/s (an FMA counts as one operation,
+    as in the per-nnz count): measured by the library's FMA microbenchmark
+    (tnlm_measure_peaks) on the device, once per process.  Returns (peak,
+    source)."""
+    if device not in _ALU_PEAK:
+        try:
+            import paper_1009_1351_gb300 as tn
+            _ALU_PEAK[device] = (tn.tnlm_measure_peaks(device)["fp32_ops"] / 1e12,
+                                 "measured: FP32 FMA microbenchmark (tnlm_measure_peaks)")
+        except Exception as exc:     # no GPU: the derived figure, said so
+            import torch
+            sms = torch.cuda.get_device_properties(device).multi_processor_count if torch.cuda.is_available() else 152
+            mhz = _peaks().get("sm_max_mhz", 2070.0)
+            _ALU_PEAK[device] = (sms * 128 * mhz * 1e6 / 1e12,
+                                 f"derived: SMs x 128 FP32 lanes x max SM clock ({exc})")
+    return _ALU_PEAK[device]
 
 
 # ---------------------------------------------------------------------------
@@ -369,8 +384,7 @@ def run_gpu(args):
             else:
                 amt = np.mean([roofline_units(c, dominant)[0] for c in cases])
                 achieved = amt / (per_launch_ms / 1e3) / 1e12
-                peak = alu_peak_tops()
-                src = "derived: 152 SMs x 128 FP32 lanes x max SM clock (1 op per lane and clock)"
+                peak, src = alu_peak_tops(local)
             traffic = measured_traffic(dominant, scenarios)
             roof = {"bound": bound, "kernel": dominant, "achieved": round(achieved, 3),
                     "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
@@ -388,7 +402,7 @@ def run_gpu(args):
             if unit_c == "GB/s":
                 ach, pk = amt_c / (ms_c / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0)
             else:
-                ach, pk = amt_c / (ms_c / 1e3) / 1e12, alu_peak_tops()
+                ach, pk = amt_c / (ms_c / 1e3) / 1e12, alu_peak_tops(local)[0]
             tr = measured_traffic(cls, scenarios)
             by_kernel[cls] = {"bound": bound_c, "achieved": round(ach, 3), "peak": round(pk, 1),
                               "unit": unit_c, "frac": round(ach / pk, 4), "launch_ms": round(ms_c, 4),

@@ -299,6 +299,18 @@ tnlm_status tnlm_profile_enable(tnlm_geometry* geom, unsigned int class_mask);
  * Synchronises the handle's device.  reset != 0 clears both afterwards. */
 tnlm_status tnlm_profile_read(tnlm_geometry* geom, double* ms, long long* launches, int reset);
 
+/* Microbenchmarks of the device's arithmetic pipes (no counterpart in the
+ * paper: they give the roofline denominators of the ALU-bound kernels).
+ * fp32_ops receives the FP32 fused multiply-add rate in lane operations per
+ * second (an FMA counted as one operation, as in the projector's count of
+ * work per matrix entry), ex2_ops the rate of ex2.approx.f32 (the special
+ * function unit the sweep's weights use); either may be NULL.  Each is the
+ * best of three timed launches after a warm-up, 8 blocks of 256 threads per
+ * SM with 8 independent dependency chains per thread, on a stream of its
+ * own; synchronises that stream and allocates (and frees) a small output
+ * buffer.  Errors: TNLM_ERR_OOM, TNLM_ERR_CUDA. */
+tnlm_status tnlm_measure_peaks(int device, double* fp32_ops, double* ex2_ops);
+
 /* Message of the last failing call on this host thread ("" if none). */
 const char* tnlm_last_error(void);
 

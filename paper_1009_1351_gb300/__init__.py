@@ -32,7 +32,7 @@ EXPORTED = ("tnlm_create_geometry", "tnlm_destroy_geometry", "tnlm_project", "tn
             "tnlm_profile_read", "tnlm_project_static", "tnlm_fbp", "tnlm_autotune",
             "tnlm_reconstruct_batch", "tnlm_batch_last_was_loop", "tnlm_fbp_phases", "tnlm_unet_create", "tnlm_unet_destroy", "tnlm_unet_param_count",
             "tnlm_unet_set_params", "tnlm_unet_get_params", "tnlm_unet_forward", "tnlm_unet_grads",
-            "tnlm_unet_adam_step", "tnlm_unet_last_error")
+            "tnlm_unet_adam_step", "tnlm_unet_last_error", "tnlm_measure_peaks")
 KCLASSES = ("prep", "project", "backproject", "cgls", "weights", "gj")
 PREC_FP32, PREC_MIXED = 0, 1
 
@@ -137,6 +137,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.tnlm_unet_adam_step.argtypes = [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                         ctypes.c_float, vp]
     lib.tnlm_unet_last_error.restype = ctypes.c_char_p
+    lib.tnlm_measure_peaks.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.tnlm_measure_peaks.restype = ctypes.c_int
     lib.tnlm_batch_last_was_loop.restype = ctypes.c_int
     lib.tnlm_last_error.restype = ctypes.c_char_p
     lib.tnlm_debug_fail_alloc_after.argtypes = [ctypes.c_int]
@@ -344,6 +347,13 @@ def tnlm_reconstruct_batch(geoms, params, ys, winvs, fs, autotune: bool = True,
 def tnlm_batch_last_was_loop() -> bool:
     """Whether the last batched call on this thread ran as one loop-graph launch."""
     return bool(load_library().tnlm_batch_last_was_loop())
+
+
+def tnlm_measure_peaks(device: int = 0) -> Dict[str, float]:
+    """Measured FP32 FMA and ex2.approx rates (lane operations per second)."""
+    a, b = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _check(load_library().tnlm_measure_peaks(int(device), ctypes.byref(a), ctypes.byref(b)))
+    return {"fp32_ops": a.value, "ex2_ops": b.value}
 
 
 def tnlm_debug_fail_alloc_after(n: int) -> None:
