@@ -283,10 +283,7 @@ def time_net(torch, tn, base: int, levels: int, batch: int, reps: int = 10) -> D
             "train_step_ms": e[1].elapsed_time(e[2]) / reps}
 
 
-def main() -> None:
-    import torch
-    import paper_1009_1351_gb300 as tn
-
+def parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--time-net", action="store_true", help="only time the network (random data)")
     ap.add_argument("--train", type=int, default=4000)
@@ -303,11 +300,16 @@ def main() -> None:
     ap.add_argument("--seed", type=int, default=7000)
     ap.add_argument("--chunk", type=int, default=64, help="slices per batched launch in the evaluation")
     ap.add_argument("--out", default=None)
-    args = ap.parse_args()
-    torch.cuda.set_device(0)
-    if args.time_net:
-        print(json.dumps(time_net(torch, tn, args.base, args.levels, args.batch)))
-        return
+    return ap
+
+
+def run(args, clocks=None):
+    """Make the data, train, evaluate cold vs warm and batched + warm vs
+    plain; returns (summary dict, held-out data, pair maker, network).
+    clocks: optional object with start() / stop() -> dict, sampled around
+    the evaluation."""
+    import torch
+    import paper_1009_1351_gb300 as tn
     maker = PairMaker(torch, tn, k_outer=args.kmax if args.target_tol > 0 else 50, tol=args.target_tol)
     t0 = time.perf_counter()
     train = maker.make(list(range(args.seed, args.seed + args.train)), keep_all=False)
@@ -349,6 +351,8 @@ def main() -> None:
     t_train = time.perf_counter() - t1
     # loss of the network's input itself (identity map) for reference
     base_loss = float(((Xt - Yt) ** 2).mean())
+    if clocks is not None:
+        clocks.start()
     rows = evaluate(torch, tn, net, maker, test, args.tol, args.kmax)
     summ = {k: float(np.mean([r[k] for r in rows])) for k in
             ("iters_cold", "iters_warm", "ms_cold", "ms_warm", "err_truth_cold", "err_truth_warm",
@@ -357,6 +361,7 @@ def main() -> None:
     bat["plain_ms"] = float(np.sum([r["ms_cold"] for r in rows]))
     bat["speedup_batched_warm_vs_plain"] = bat["plain_ms"] / bat["batched_warm_ms"]
     bat["speedup_batched_cold_vs_plain"] = bat["plain_ms"] / bat["batched_cold_ms"]
+    clk = clocks.stop() if clocks is not None else None
     ti = train.get("target_iters", [])
     out = {"train": args.train, "test": args.test, "epochs": args.epochs, "batch": args.batch,
            "target": (f"TNLM to tol {args.target_tol} (mean {np.mean(ti):.1f} iterations)" if ti
@@ -364,7 +369,20 @@ def main() -> None:
            "net": {"base": args.base, "levels": args.levels, "params": net.param_count},
            "seconds": {"data": round(t_data, 1), "train": round(t_train, 1)},
            "loss": hist, "identity_test_loss": base_loss, "tol": args.tol,
-           "mean": summ, "batched": bat, "per_slice": rows}
+           "mean": summ, "batched": bat, "clocks": clk, "per_slice": rows}
+    return out, test, maker, net
+
+
+def main() -> None:
+    import torch
+    import paper_1009_1351_gb300 as tn
+
+    args = parser().parse_args()
+    torch.cuda.set_device(0)
+    if args.time_net:
+        print(json.dumps(time_net(torch, tn, args.base, args.levels, args.batch)))
+        return
+    out, _, _, _ = run(args)
     print(json.dumps({k: v for k, v in out.items() if k != "per_slice"}))
     if args.out:
         with open(args.out, "w") as fh:
