@@ -8,8 +8,8 @@ Runs the library's warm-start study (paper_1009_1351_gb300.warmstart.run:
 pairs made by the plain method on the GPU, training by the library's own
 kernels, held-out slices run cold and warm to the same stopping tolerance,
 then the batched + warm form against the plain form), with nvidia-smi clocks
-sampled during the evaluation.  Then, for the first --oracle-slices held-out
-slices (the dose scenarios in turn), the FP64 oracle runs from the same cold
+sampled during the evaluation.  Then, for --oracle-slices held-out slices
+(the first of each dose scenario in turn), the FP64 oracle runs from the same cold
 and warm start images for the same number of outer iterations as the GPU
 took, and the relative L2 error of each GPU result against it is recorded.
 """
@@ -41,7 +41,15 @@ def main():
     out, test, maker, net = warmstart.run(args, clocks=bench.ClockSampler(0))
     t0 = time.perf_counter()
     rows = []
-    for i in range(min(args.oracle_slices, len(test["seed"]))):
+    # the first held-out slice of each dose scenario in turn
+    order, seen = [], {}
+    for i, sc in enumerate(test["scenario"]):
+        seen.setdefault(sc, []).append(i)
+    while len(order) < min(args.oracle_slices, len(test["seed"])):
+        for sc in list(seen):
+            if seen[sc] and len(order) < args.oracle_slices:
+                order.append(seen[sc].pop(0))
+    for i in order:
         c = maker.cases[test["scenario"][i]]
         G = oracle.Geom(c.geom)
         y = test["y"][i].double().cpu().numpy().astype(np.float32)
