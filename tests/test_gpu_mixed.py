@@ -81,7 +81,7 @@ def test_mixed_distances_match_oracle(tn, oracle_mod, shape, d, W):
     np.testing.assert_allclose(norm[3], norm32[3], rtol=1e-3)
 
 
-@pytest.mark.parametrize("name,k", [("tiny", 20), ("mid_c", 3), ("large_b", 3)])
+@pytest.mark.parametrize("name,k", [("tiny", 20), ("mid_c", 3), ("mid_c", 50), ("large_b", 3)])
 def test_mixed_reconstruction_matches_oracle(tn, oracle_mod, name, k):
     c = synth.case(name)
     d = synth.make_inputs(c)
