@@ -588,11 +588,8 @@ __device__ __forceinline__ bool consumer_sync_or(bool v) {
     return r != 0;
 }
 
-#ifndef TNLM_GJ_CTAS
-#define TNLM_GJ_CTAS 3
-#endif
 template <int W, int MODE>
-__global__ void __launch_bounds__(kTmaThreads, TNLM_GJ_CTAS) k_gj_tma(GjArgs a, const __grid_constant__ CUtensorMap tmF,
+__global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __grid_constant__ CUtensorMap tmF,
                                                         const __grid_constant__ CUtensorMap tmB,
                                                         const __grid_constant__ CUtensorMap tmU,
                                                         int tpb, int split, float4* __restrict__ hsum,
