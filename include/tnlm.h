@@ -97,6 +97,12 @@ typedef struct {
                         ends with one more projection for the data term of the final
                         image (see tnlm_report); costs one more pass over the stored
                         distances per iteration.  0: off */
+    int recompute;   /* 1: the Gauss-Jacobi sweeps recompute the Eq. 8 patch distances of
+                        both directions from g^(k) in every sweep instead of reading the
+                        distance array the weights step stores (that step then only forms
+                        the row minima); same arithmetic, FP32 summation order may differ
+                        in the last bit; FP32 only, patch <= 7, window <= 15.  0: store
+                        the distances once per outer iteration and stream them (default) */
 } tnlm_params;
 
 enum { TNLM_PREC_FP32 = 0, TNLM_PREC_MIXED = 1 };

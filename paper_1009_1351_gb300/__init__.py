@@ -51,7 +51,7 @@ class ParamsC(ctypes.Structure):
                 ("m2", ctypes.c_int), ("k_outer", ctypes.c_int), ("data_step", ctypes.c_int),
                 ("clamp", ctypes.c_int), ("tol", ctypes.c_double),
                 ("tol_check_every", ctypes.c_int), ("precision", ctypes.c_int),
-                ("monitor", ctypes.c_int)]
+                ("monitor", ctypes.c_int), ("recompute", ctypes.c_int)]
 
 
 class ReportC(ctypes.Structure):
@@ -196,7 +196,8 @@ def params_c(p: Any) -> ParamsC:
                    int(p.window), int(p.m1), int(p.m2), int(p.k_outer),
                    int(getattr(p, "data_step", 0)), int(getattr(p, "clamp", 1)),
                    float(getattr(p, "tol", 0.0)), int(getattr(p, "tol_check_every", 1)),
-                   int(getattr(p, "precision", PREC_FP32)), int(getattr(p, "monitor", 0)))
+                   int(getattr(p, "precision", PREC_FP32)), int(getattr(p, "monitor", 0)),
+                   int(getattr(p, "recompute", 0)))
 
 
 class Geometry:

@@ -142,6 +142,11 @@ tnlm_status check_params(const tnlm_params* p) {
     if (p->precision == TNLM_PREC_MIXED && !weights_tc_supported(p->patch, p->window))
         return fail(TNLM_ERR_INVALID_ARG, "mixed precision supports patch <= 7 and window in [3, 15]");
     if (p->monitor != 0 && p->monitor != 1) return fail(TNLM_ERR_INVALID_ARG, "monitor must be 0 or 1");
+    if (p->recompute != 0 && p->recompute != 1) return fail(TNLM_ERR_INVALID_ARG, "recompute must be 0 or 1");
+    if (p->recompute && p->precision == TNLM_PREC_MIXED)
+        return fail(TNLM_ERR_INVALID_ARG, "recompute takes the FP32 distances (precision must be TNLM_PREC_FP32)");
+    if (p->recompute && !fused_supported(p->patch, p->window))
+        return fail(TNLM_ERR_INVALID_ARG, "recompute supports patch <= 7 and window <= 15");
     return TNLM_OK;
 }
 
@@ -322,10 +327,20 @@ tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float*
     if (p->m2 > 0 || p->monitor) {
         if (p->precision == TNLM_PREC_MIXED)
             LK(TNLM_KCLASS_WEIGHTS, launch_weights_tc(g, ws, p->patch, p->window, ws.u, st), "weights (tensor cores)");
-        else
-            LK(TNLM_KCLASS_WEIGHTS, launch_weights(g, ws, p->patch, p->window, ws.u, st), "weights");
+        else    // with recompute only the row minima are needed (the monitor reads the distances)
+            LK(TNLM_KCLASS_WEIGHTS,
+               launch_weights(g, ws, p->patch, p->window, ws.u, st, !(p->recompute && !p->monitor)), "weights");
     }
-    if (p->m2 > 0) {
+    if (p->m2 > 0 && p->recompute) {
+        float* bufs[2] = {ws.U0, ws.U1};
+        for (int m = 0; m < p->m2; ++m) {
+            const bool last = m == p->m2 - 1;
+            LK(TNLM_KCLASS_GJ, launch_gj_fused(g, ws, p->patch, p->window, p->h, p->mu_hat, ws.u, bufs[m & 1],
+                                               last ? nullptr : bufs[(m + 1) & 1], last ? d_f : nullptr,
+                                               p->clamp, st),
+               "gauss-jacobi (distances recomputed)");
+        }
+    } else if (p->m2 > 0) {
         float* bufs[2] = {ws.U0, ws.U1};
         for (int m = 0; m < p->m2; ++m) {
             const bool last = m == p->m2 - 1;
@@ -376,7 +391,8 @@ struct GraphState {
 bool same_shape(const tnlm_params& a, const tnlm_params& b) {
     return a.mu_hat == b.mu_hat && a.h == b.h && a.beta == b.beta && a.patch == b.patch &&
            a.window == b.window && a.m1 == b.m1 && a.m2 == b.m2 && a.data_step == b.data_step &&
-           a.clamp == b.clamp && a.precision == b.precision && a.monitor == b.monitor;
+           a.clamp == b.clamp && a.precision == b.precision && a.monitor == b.monitor &&
+           a.recompute == b.recompute;
 }
 
 tnlm_status ensure_graph(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f) {
@@ -1023,6 +1039,7 @@ tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* d, tnlm_geometry** ou
     e = prepare_backproject(&g->cta_slots_bp);
     if (e == cudaSuccess) e = prepare_weights(&g->cta_slots_gj);
     if (e == cudaSuccess) e = prepare_weights_tc();
+    if (e == cudaSuccess) e = prepare_gj_fused();
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) {
         tnlm_destroy_geometry(g);

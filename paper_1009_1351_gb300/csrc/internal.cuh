@@ -183,8 +183,17 @@ cudaError_t launch_sqrt(const float* w, float* sw, size_t n, int* err, cudaStrea
 cudaError_t launch_fill(float* p, float v, size_t n, cudaStream_t st);
 
 // TNLM step kernels
+// store = false: only the row minima (and u^(0)) -- the distances are
+// recomputed by the fused sweep
 cudaError_t launch_weights(const tnlm_geometry* g, const Workspace& ws, int patch, int window,
-                           const float* gimg, cudaStream_t st);
+                           const float* gimg, cudaStream_t st, bool store = true);
+// Gauss-Jacobi sweep that recomputes the patch distances of both directions
+// from g instead of reading the stored array (fout != NULL: the last sweep)
+cudaError_t launch_gj_fused(const tnlm_geometry* g, const Workspace& ws, int patch, int window, double h,
+                            double mu_hat, const float* gimg, const float* uin, float* uout, float* fout,
+                            int clamp, cudaStream_t st);
+cudaError_t prepare_gj_fused();
+bool fused_supported(int patch, int window);
 cudaError_t launch_gj_sweep(const tnlm_geometry* g, const Workspace& ws, int window, double h,
                             double mu_hat, const float* gimg, const float* uin, float* uout,
                             float* fout, int clamp, cudaStream_t st);

@@ -160,7 +160,9 @@ __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
 #pragma unroll
     for (int r = 0; r < G::RPT; ++r) mf[r] = INFINITY;
     const size_t plane = a.pp.plane;
-    float* Dbase = a.D + (size_t)p * W * W * plane + (size_t)(Y0 + r2 + a.pp.oy) * a.pp.px + x2 + a.pp.ox;
+    const bool store = a.D != nullptr;            // NULL: row minima (and u^(0)) only
+    float* Dbase = store ? a.D + (size_t)p * W * W * plane + (size_t)(Y0 + r2 + a.pp.oy) * a.pp.px + x2 + a.pp.ox
+                         : nullptr;
 
     horizontal(-rho, -rho, H);
     __syncthreads();
@@ -190,7 +192,7 @@ __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
             // (3) store the forward distance (+inf where x + s leaves the image),
             //     track the forward row minimum and the backward minimum at x + s
             const bool colok = xin && (unsigned)(x2 + sx) < (unsigned)nx;
-            float* Dk = Dbase + (size_t)k * plane;
+            float* Dk = store ? Dbase + (size_t)k * plane : nullptr;
             float* bm = BM + (r2 + sy + rho) * G::BMW + c2 + sx + rho;
             const int y0 = Y0 + r2;
             if (y0 + G::RPT <= ny && y0 + sy >= 0 && y0 + G::RPT - 1 + sy < ny) {
@@ -198,7 +200,7 @@ __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
 #pragma unroll
                 for (int r = 0; r < G::RPT; ++r) {
                     const float val = colok ? dv[r] : INFINITY;
-                    if (xin) Dk[(size_t)r * a.pp.px] = val;
+                    if (xin && store) Dk[(size_t)r * a.pp.px] = val;
                     mf[r] = fminf(mf[r], val);
                     bm[r * G::BMW] = fminf(bm[r * G::BMW], val);
                 }
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
                     const bool yin = y < ny;
                     const bool vf = colok && yin && (unsigned)(y + sy) < (unsigned)ny;
                     const float val = vf ? dv[r] : INFINITY;
-                    if (xin && yin) Dk[(size_t)r * a.pp.px] = val;
+                    if (xin && yin && store) Dk[(size_t)r * a.pp.px] = val;
                     mf[r] = fminf(mf[r], val);
                     bm[r * G::BMW] = fminf(bm[r * G::BMW], val);
                 }
@@ -269,9 +271,9 @@ static cudaError_t launch_weights_r(const WArgs& a, cudaStream_t st) {
 }
 
 cudaError_t launch_weights(const tnlm_geometry* g, const Workspace& ws, int patch, int window,
-                           const float* gimg, cudaStream_t st) {
+                           const float* gimg, cudaStream_t st, bool store) {
     WArgs a;
-    a.g = gimg; a.D = ws.D; a.mins = ws.mins; a.U0 = ws.U0; a.err = ws.st.err; a.pp = ws.pp;
+    a.g = gimg; a.D = store ? ws.D : nullptr; a.mins = ws.mins; a.U0 = ws.U0; a.err = ws.st.err; a.pp = ws.pp;
     a.nx = g->nx; a.ny = g->ny; a.N = g->N; a.rho = (window - 1) / 2; a.W = window;
     // backward minima start above every distance (0x7f7f7f7f = 3.4e38)
     const size_t npx = (size_t)g->nx * g->ny;
@@ -1270,6 +1272,293 @@ cudaError_t launch_weights_export(const tnlm_geometry* g, const Workspace& ws, i
     k_weights_export<<<(int)b, 256, 0, st>>>(ws.D, ws.mins, ws.zn, d_dist, d_norm, ws.pp, g->nx,
                                              g->ny, g->N, window * window);
     return cudaGetLastError();
+}
+
+
+// ---------------------------------------------------------------------------
+// Gauss-Jacobi sweep with the patch distances recomputed (the alternative to
+// storing them: no distance array is read).  A block owns a 64 x TY tile of
+// one phase i, the tiles of K4 (k_weights).  It stages g_i with the patch
+// halo, g_{i+1} and g_{i-1} with the window and patch halo and the two
+// neighbour iterates u_{i+1}, u_{i-1} with the window halo; for every shift
+// s it forms, exactly as K4 does (horizontal running sums of the squared
+// differences into one of two buffers, vertical sums of the other, one
+// barrier per shift), the forward distance D_i(x, s) = |P_i(x) - P_{i+1}(x+s)|^2
+// and the backward one D_{i-1}(x-s, s) = |P_{i-1}(x-s) - P_i(x)|^2 of the
+// thread's pixels, weights them with the stored row minima,
+//   e = 2^(log2(e) (m - D) / h^2),
+// and accumulates both directions' sums and normalisers in registers.  The
+// backward distance is summed around x rather than around x - s, so its FP32
+// association can differ from K4's in the last bit.
+// ---------------------------------------------------------------------------
+struct FArgs {
+    const float* g;       // g^(k) [N][ny][nx]
+    const float* mins;    // [2][N][ny][nx] row minima (toward i+1, toward i-1)
+    const float* uin;     // padded iterate planes [N][py][px], zero outside the image
+    float* uout;          // padded (intermediate sweeps)
+    float* fout;          // unpadded result (last sweep)
+    double* part;         // last sweep: kPart partials per block
+    int* err;
+    PadPlane pp;
+    int nx, ny, N, rho, W, clamp;
+    float k2, c1, c2;
+};
+
+template <int R>
+struct FGeo {
+    using G = WGeo<R>;
+    int GJW, GJH, GJS, UW, UH, US;
+    __host__ __device__ explicit FGeo(int rho) {
+        GJW = (G::TX + 2 * rho + 2 * R) | 1;
+        GJH = G::TY + 2 * rho + 2 * R;
+        GJS = (GJW * GJH + 3) / 4 * 4;
+        UW = G::TX + 2 * rho;
+        UH = G::TY + 2 * rho;
+        US = (UW * UH + 3) / 4 * 4;
+    }
+    __host__ __device__ size_t floats() const {
+        return (size_t)G::GIW * G::GIH + 2 * (size_t)GJS + 4 * 32 * (size_t)G::HP + 2 * (size_t)US;
+    }
+};
+
+template <int R, int MODE>
+__global__ void __launch_bounds__(256, 2) k_gj_fused(FArgs a) {
+    using G = WGeo<R>;
+    extern __shared__ __align__(16) float sm[];
+    const int rho = a.rho, W = a.W, N = a.N, nx = a.nx, ny = a.ny;
+    const FGeo<R> L(rho);
+    float* Gi = sm;                                  // g_i at rows Y0-R.., columns X0-R..
+    float* Gn = Gi + G::GIW * G::GIH;                // g_{i+1} at rows Y0-rho-R.., columns X0-rho-R..
+    float* Gp = Gn + L.GJS;                          // g_{i-1}, same region
+    float* H = Gp + L.GJS;                           // [buffer][direction][32][HP]
+    float* Un = H + 4 * 32 * G::HP;                  // u_{i+1} at rows Y0-rho.., columns X0-rho..
+    float* Up = Un + L.US;                           // u_{i-1}, same region
+    const int i = blockIdx.z, inx = (i + 1) % N, ip = (i + N - 1) % N;
+    const int X0 = blockIdx.x * G::TX, Y0 = blockIdx.y * G::TY;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const size_t npx = (size_t)nx * ny;
+    const float* gi = a.g + i * npx;
+    const float* gn = a.g + inx * npx;
+    const float* gp = a.g + ip * npx;
+    for (int r = warp; r < G::GIH; r += 8)
+        for (int c = lane; c < G::GIW; c += 32) {
+            const int x = X0 - R + c, y = Y0 - R + r;
+            Gi[r * G::GIW + c] = (x >= 0 && x < nx && y >= 0 && y < ny) ? gi[(size_t)y * nx + x] : 0.f;
+        }
+    for (int r = warp; r < L.GJH; r += 8)
+        for (int c = lane; c < L.GJW; c += 32) {
+            const int x = X0 - rho - R + c, y = Y0 - rho - R + r;
+            const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
+            Gn[r * L.GJW + c] = in ? gn[(size_t)y * nx + x] : 0.f;
+            Gp[r * L.GJW + c] = in ? gp[(size_t)y * nx + x] : 0.f;
+        }
+    const size_t plane = a.pp.plane;
+    for (int r = warp; r < L.UH; r += 8)
+        for (int c = lane; c < L.UW; c += 32) {
+            const int x = X0 - rho + c, y = Y0 - rho + r;
+            const bool in = x >= 0 && x < nx && y >= 0 && y < ny;
+            const size_t o = (size_t)(y + a.pp.oy) * a.pp.px + x + a.pp.ox;
+            Un[r * L.UW + c] = in ? a.uin[inx * plane + o] : 0.f;
+            Up[r * L.UW + c] = in ? a.uin[ip * plane + o] : 0.f;
+        }
+    __syncthreads();
+
+    // pass-1 task: H row hr, 8 adjacent columns from g8
+    const int g8 = 8 * ((warp & 1) * 4 + (lane & 3));
+    const int hr = (warp >> 1) * 8 + (lane >> 2);
+    // pass-2 task: output column c2, output rows r2 .. r2 + RPT - 1
+    const int c2 = (warp & 1) * 32 + lane;
+    const int r2 = (warp >> 1) * G::RPT;
+    const int x2 = X0 + c2;
+    const bool xin = x2 < nx;
+
+    // horizontal patch sums of direction dir (0: g_{i+1} at +s, 1: g_{i-1} at -s)
+    auto horizontal = [&](const float* Gj, int sx, int sy, float* Hb) {
+        if (hr >= G::HR) return;
+        float d2[4 * G::NQ4];
+        const float* pi = Gi + hr * G::GIW + g8;
+        const float* pj = Gj + (hr + sy + rho) * L.GJW + g8 + sx + rho;
+#pragma unroll
+        for (int t = 0; t < G::NQ4; ++t) {
+            const float4 v = *(const float4*)(pi + 4 * t);
+            const float vi[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (4 * t + u < G::NQ) {
+                    const float d = vi[u] - pj[4 * t + u];
+                    d2[4 * t + u] = d * d;
+                }
+            }
+        }
+        float h[8];
+#pragma unroll
+        for (int c = 0; c < 8; c += 2) {
+            float m = 0.f;
+#pragma unroll
+            for (int t = 1; t <= 2 * R; ++t) m = (t == 1) ? d2[c + 1] : m + d2[c + t];
+            h[c] = (R == 0) ? d2[c] : d2[c] + m;
+            h[c + 1] = (R == 0) ? d2[c + 1] : m + d2[c + 2 * R + 1];
+        }
+        float* o = Hb + hr * G::HP + g8;
+        *(float4*)o = make_float4(h[0], h[1], h[2], h[3]);
+        *(float4*)(o + 4) = make_float4(h[4], h[5], h[6], h[7]);
+    };
+    // vertical sums of a buffer: this thread's RPT distances
+    auto vertical = [&](const float* Hb, float* dv) {
+        const float* hb = Hb + r2 * G::HP + c2;
+        float hv[G::RPT + 2 * R];
+#pragma unroll
+        for (int t = 0; t < G::RPT + 2 * R; ++t) hv[t] = hb[t * G::HP];
+#pragma unroll
+        for (int r = 0; r < G::RPT; r += 2) {
+            float m = 0.f;
+#pragma unroll
+            for (int t = 1; t <= 2 * R; ++t) m = (t == 1) ? hv[r + 1] : m + hv[r + t];
+            dv[r] = (R == 0) ? hv[r] : hv[r] + m;
+            if (r + 1 < G::RPT) dv[r + 1] = (R == 0) ? hv[r + 1] : m + hv[r + 2 * R + 1];
+        }
+    };
+
+    const float k2 = a.k2;
+    float mfk[G::RPT], mbk[G::RPT], af[G::RPT], zf[G::RPT], ab[G::RPT], zb[G::RPT];
+#pragma unroll
+    for (int r = 0; r < G::RPT; ++r) {
+        const int y = Y0 + r2 + r;
+        const bool in = xin && y < ny;
+        const size_t pix = (size_t)y * nx + x2;
+        mfk[r] = in ? a.mins[i * npx + pix] * k2 : 0.f;
+        mbk[r] = in ? a.mins[(N + i) * npx + pix] * k2 : 0.f;
+        af[r] = zf[r] = ab[r] = zb[r] = 0.f;
+    }
+    const int HB = 32 * G::HP;                       // one direction's buffer
+    horizontal(Gn, -rho, -rho, H);
+    horizontal(Gp, rho, rho, H + HB);
+    __syncthreads();
+    const int W2 = W * W;
+    int sx = -rho, sy = -rho;
+    for (int k = 0; k < W2; ++k) {
+        if (k + 1 < W2) {
+            const int nx1 = (sx == rho) ? -rho : sx + 1;
+            const int ny1 = (sx == rho) ? sy + 1 : sy;
+            float* Hn = H + ((k + 1) & 1) * 2 * HB;
+            horizontal(Gn, nx1, ny1, Hn);
+            horizontal(Gp, -nx1, -ny1, Hn + HB);
+        }
+        float df[G::RPT], db[G::RPT];
+        const float* Hc = H + (k & 1) * 2 * HB;
+        vertical(Hc, df);
+        vertical(Hc + HB, db);
+        const bool fcol = xin && (unsigned)(x2 + sx) < (unsigned)nx;
+        const bool bcol = xin && (unsigned)(x2 - sx) < (unsigned)nx;
+        const float* un = Un + (r2 + sy + rho) * L.UW + c2 + sx + rho;
+        const float* up = Up + (r2 - sy + rho) * L.UW + c2 - sx + rho;
+#pragma unroll
+        for (int r = 0; r < G::RPT; ++r) {
+            const int y = Y0 + r2 + r;
+            const bool yin = y < ny;
+            if (fcol && yin && (unsigned)(y + sy) < (unsigned)ny) {
+                const float e = ex2_approx(fmaf(-df[r], k2, mfk[r]));
+                af[r] = fmaf(e, un[r * L.UW], af[r]);
+                zf[r] += e;
+            }
+            if (bcol && yin && (unsigned)(y - sy) < (unsigned)ny) {
+                const float e = ex2_approx(fmaf(-db[r], k2, mbk[r]));
+                ab[r] = fmaf(e, up[r * L.UW], ab[r]);
+                zb[r] += e;
+            }
+        }
+        __syncthreads();
+        if (sx == rho) { sx = -rho; ++sy; } else { ++sx; }
+    }
+    float dsq = 0.f, nsq = 0.f, ncl = 0.f;
+    bool bad = false;
+#pragma unroll
+    for (int r = 0; r < G::RPT; ++r) {
+        const int y = Y0 + r2 + r;
+        if (!xin || y >= ny) continue;
+        bad |= !(zf[r] >= 0.5f) || !(zb[r] >= 0.5f);
+        const size_t pix = (size_t)y * nx + x2;
+        const float unew = fmaf(a.g[i * npx + pix], a.c1, a.c2 * (af[r] / zf[r] + ab[r] / zb[r]));
+        if (MODE == 0) {
+            a.uout[i * plane + (size_t)(y + a.pp.oy) * a.pp.px + x2 + a.pp.ox] = unew;
+        } else {
+            const float fnew = a.clamp ? fmaxf(unew, 0.f) : unew;
+            if (a.clamp && unew < 0.f) ncl += 1.f;
+            const float fold = a.fout[i * npx + pix];
+            a.fout[i * npx + pix] = fnew;
+            dsq = fmaf(fnew - fold, fnew - fold, dsq);
+            nsq = fmaf(fnew, fnew, nsq);
+        }
+    }
+    if (bad) atomicOr(a.err, 8);
+    if (MODE == 1) {
+        __shared__ double sh[8];
+        const double d2 = block_sum<256>(dsq, sh, tid);
+        const double n2 = block_sum<256>(nsq, sh, tid);
+        const double c3 = block_sum<256>(ncl, sh, tid);
+        if (tid == 0) {
+            const size_t blk = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+            a.part[kPart * blk] = d2;
+            a.part[kPart * blk + 1] = n2;
+            a.part[kPart * blk + 2] = c3;
+        }
+    }
+}
+
+template <int R>
+static size_t fused_smem(int rho) { return sizeof(float) * FGeo<R>(rho).floats(); }
+
+cudaError_t prepare_gj_fused() {
+    cudaError_t e = cudaSuccess;
+#define TNLM_PREP_F(R)                                                                              \
+    if (e == cudaSuccess)                                                                           \
+        e = cudaFuncSetAttribute(k_gj_fused<R, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                 (int)fused_smem<R>((kMaxWindow - 1) / 2));                         \
+    if (e == cudaSuccess)                                                                           \
+        e = cudaFuncSetAttribute(k_gj_fused<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,     \
+                                 (int)fused_smem<R>((kMaxWindow - 1) / 2));
+    TNLM_PREP_F(0) TNLM_PREP_F(1) TNLM_PREP_F(2) TNLM_PREP_F(3)
+#undef TNLM_PREP_F
+    return e;
+}
+
+template <int R>
+static cudaError_t launch_fused_r(const tnlm_geometry* g, const FArgs& a, cudaStream_t st) {
+    using G = WGeo<R>;
+    dim3 grid((g->nx + G::TX - 1) / G::TX, (g->ny + G::TY - 1) / G::TY, g->N);
+    const size_t sm = fused_smem<R>(a.rho);
+    if (a.fout) k_gj_fused<R, 1><<<grid, 256, sm, st>>>(a);
+    else k_gj_fused<R, 0><<<grid, 256, sm, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    // the partial slots this launch does not write must read as zero
+    const size_t nb = (size_t)grid.x * grid.y * grid.z, nmax = (size_t)gj_blocks(g);
+    if (e == cudaSuccess && a.fout && nmax > nb)
+        e = cudaMemsetAsync(a.part + kPart * nb, 0, 8 * kPart * (nmax - nb), st);
+    return e;
+}
+
+bool fused_supported(int patch, int window) {
+    return patch >= 1 && patch <= 7 && (patch & 1) && window >= 1 && window <= 15 && (window & 1);
+}
+
+cudaError_t launch_gj_fused(const tnlm_geometry* g, const Workspace& ws, int patch, int window, double h,
+                            double mu_hat, const float* gimg, const float* uin, float* uout, float* fout,
+                            int clamp, cudaStream_t st) {
+    if (!fused_supported(patch, window)) return cudaErrorInvalidValue;
+    FArgs a;
+    a.g = gimg; a.mins = ws.mins; a.uin = uin; a.uout = uout; a.fout = fout; a.part = ws.part2;
+    a.err = ws.st.err; a.pp = ws.pp;
+    a.nx = g->nx; a.ny = g->ny; a.N = g->N; a.rho = (window - 1) / 2; a.W = window; a.clamp = clamp;
+    a.k2 = (float)(1.4426950408889634 / (h * h));
+    a.c1 = (float)(1.0 / (mu_hat + 1.0));
+    a.c2 = (float)(mu_hat / (2.0 * mu_hat + 2.0));
+    switch ((patch - 1) / 2) {
+        case 0: return launch_fused_r<0>(g, a, st);
+        case 1: return launch_fused_r<1>(g, a, st);
+        case 2: return launch_fused_r<2>(g, a, st);
+        case 3: return launch_fused_r<3>(g, a, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace tnlm

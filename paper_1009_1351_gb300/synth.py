@@ -76,6 +76,7 @@ class Params:
     clamp: int = 1            # positivity truncation after each outer iteration
     precision: int = 0        # 0: FP32; 1: split-FP16 tensor-core patch cross terms
     monitor: int = 0          # 1: FP64 TNLM term / objective of Eq. 1 every iteration
+    recompute: int = 0        # 1: sweeps recompute the patch distances (no stored array)
 
 
 @dataclasses.dataclass(frozen=True)
