@@ -192,7 +192,7 @@ WsLayout ws_layout(const tnlm_geometry* g, int rho, int kcap) {
     L.off_U1 = take(4 * L.pp.plane * N);
     L.off_mins = take(4 * 2 * npx * N);
     L.off_zn = take(4 * 2 * npx * N);
-    L.part_len = N * (size_t)g->V * proj_chunks(g) + N * (size_t)bp_blocks_per_phase(g);
+    L.part_len = N * (size_t)proj_blocks_per_phase(g) + N * (size_t)bp_blocks_per_phase(g);
     L.part2_len = 3 * (size_t)gj_blocks(g);
     L.off_part = take(8 * L.part_len);
     L.off_part2 = take(8 * L.part2_len);
@@ -284,7 +284,7 @@ tnlm_status check_geom_handle(const tnlm_geometry* g) {
 tnlm_status outer_iteration(tnlm_geometry* g, const tnlm_params* p, const float* d_y, float* d_f,
                             cudaStream_t st) {
     Workspace& ws = g->ws;
-    const size_t nps = (size_t)g->N * g->V * proj_chunks(g);
+    const size_t nps = (size_t)g->N * proj_blocks_per_phase(g);
     double* part_s = ws.part;
     double* part_i = ws.part + nps;
     // ---- data step: r0 = sqrt(w)(y - P f), s0 = P_n^T r0 (CGLS) / w(y - P f) back-projected (Eq. 4)
@@ -366,7 +366,7 @@ tnlm_status final_data_term(tnlm_geometry* g, const float* d_y, const float* d_f
     ProjOut o{};
     o.mode = 1; o.r = ws.r; o.z = ws.z; o.y = d_y; o.sw = ws.sw; o.part = ws.part;
     LK(TNLM_KCLASS_PROJECT, launch_project(g, ws.R, ws.T, o, st), "project");
-    LK(TNLM_KCLASS_CGLS, launch_sum_partials(ws.part, g->N * g->V * proj_chunks(g), ws.st.res_final, st),
+    LK(TNLM_KCLASS_CGLS, launch_sum_partials(ws.part, g->N * proj_blocks_per_phase(g), ws.st.res_final, st),
        "data term");
     return TNLM_OK;
 }

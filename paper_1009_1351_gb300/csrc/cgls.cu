@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kScalarThreads) k_cgls_b(ScalArgs a) {
 static ScalArgs scal_args(const tnlm_geometry* g, const Workspace& ws) {
     ScalArgs a;
     a.part_s = ws.part;
-    a.ps = g->V * proj_chunks(g);
+    a.ps = proj_blocks_per_phase(g);
     a.part_i = ws.part + (size_t)g->N * a.ps;
     a.pi = bp_blocks_per_phase(g);
     a.st = ws.st;

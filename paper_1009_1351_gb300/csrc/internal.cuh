@@ -28,7 +28,7 @@ namespace tnlm {
 
 constexpr int kMaxPatch = 15;
 constexpr int kMaxWindow = 31;
-constexpr int kProjThreads = 256;     // rays per projector block (one view)
+constexpr int kProjThreads = 256;     // rays per projector block
 constexpr int kWTileX = 32, kWTileY = 16;  // weight kernel output tile
 constexpr int kGjTileX = 32, kGjTileY = 8; // Gauss-Jacobi tile
 
@@ -139,7 +139,7 @@ struct ProjOut {
     const float* sw;       // modes 1, 2
     double* part;          // modes 1, 2: [N*V*nchunk] partial sums of squares
 };
-int proj_chunks(const tnlm_geometry* g);
+int proj_blocks_per_phase(const tnlm_geometry* g);
 cudaError_t launch_prep_dual(const tnlm_geometry* g, const float* img, float* R, float* T,
                              cudaStream_t st);
 cudaError_t launch_prep_dual_copy(const tnlm_geometry* g, const float* img, float* cp, float* R,
