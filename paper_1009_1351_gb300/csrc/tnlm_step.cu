@@ -75,7 +75,13 @@ struct WGeo {
     }
 };
 
-template <int R>
+// SLIDE (patch <= 7, window <= 15): pass 1 keeps the task's g_p segment in
+// registers for the whole kernel and, along a row of shifts (sy fixed, sx
+// rising), a sliding register window of the g_q segment that takes one new
+// value per shift; the shift loop is unrolled over sx so every window index
+// is static.  Otherwise pass 1 reloads both segments from shared memory for
+// every shift.
+template <int R, bool SLIDE>
 __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
     using G = WGeo<R>;
     extern __shared__ __align__(16) float sm[];
@@ -164,19 +170,12 @@ __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
     float* Dbase = store ? a.D + (size_t)p * W * W * plane + (size_t)(Y0 + r2 + a.pp.oy) * a.pp.px + x2 + a.pp.ox
                          : nullptr;
 
-    horizontal(-rho, -rho, H);
-    __syncthreads();
-    const int W2 = W * W;
-    int sx = -rho, sy = -rho;
-    for (int k = 0; k < W2; ++k) {
-        if (k + 1 < W2) {
-            const int nx1 = (sx == rho) ? -rho : sx + 1;
-            const int ny1 = (sx == rho) ? sy + 1 : sy;
-            horizontal(nx1, ny1, H + ((k + 1) & 1) * 32 * G::HP);
-        }
-        // (2) vertical sums: D(c2, r) = sum_{t=0..2R} H(r + t, c2)
+    // (2) vertical sums of the shift with index k = (sy + rho) W + sx + rho
+    //     from buffer Hk, the stores and both minima
+    auto vertical = [&](int k, int sx, int sy, const float* Hk) {
+        // D(c2, r) = sum_{t=0..2R} H(r + t, c2)
         {
-            const float* Hb = H + (k & 1) * 32 * G::HP + r2 * G::HP + c2;
+            const float* Hb = Hk + r2 * G::HP + c2;
             float hv[G::RPT + 2 * R];
 #pragma unroll
             for (int t = 0; t < G::RPT + 2 * R; ++t) hv[t] = Hb[t * G::HP];
@@ -217,8 +216,77 @@ __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
                 }
             }
         }
+    };
+
+    const int W2 = W * W;
+    if constexpr (SLIDE) {
+        // g_p segment of the pass-1 task, for every shift
+        const bool hact = hr < G::HR;
+        float gi[4 * G::NQ4];
+#pragma unroll
+        for (int t = 0; t < G::NQ4; ++t) {
+            const float4 v = hact ? *(const float4*)(Gi + hr * G::GIW + g8 + 4 * t)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+            gi[4 * t] = v.x; gi[4 * t + 1] = v.y; gi[4 * t + 2] = v.z; gi[4 * t + 3] = v.w;
+        }
+        float gw[G::NQ];   // g_q(row, g8 + sx + rho + t) in slot (sx + rho + t) % NQ
+        int k = 0;
+        for (int sy = -rho; sy <= rho; ++sy) {
+            const float* prow = Gj + (hr + sy + rho) * L.GJW + g8;
+#pragma unroll
+            for (int j = 0; j < 15; ++j) {   // 15 = the largest window of this path
+                if (j >= W) break;
+                if (hact) {
+                    if (j == 0) {
+#pragma unroll
+                        for (int t = 0; t < G::NQ - 1; ++t) gw[t] = prow[t];
+                    }
+                    gw[(j + G::NQ - 1) % G::NQ] = prow[j + G::NQ - 1];
+                    float d2[G::NQ];
+#pragma unroll
+                    for (int t = 0; t < G::NQ; ++t) {
+                        const float d = gi[t] - gw[(j + t) % G::NQ];
+                        d2[t] = d * d;
+                    }
+                    float h[8];
+#pragma unroll
+                    for (int c = 0; c < 8; c += 2) {
+                        float m = 0.f;
+#pragma unroll
+                        for (int t = 1; t <= 2 * R; ++t) m = (t == 1) ? d2[c + 1] : m + d2[c + t];
+                        h[c] = (R == 0) ? d2[c] : d2[c] + m;
+                        h[c + 1] = (R == 0) ? d2[c + 1] : m + d2[c + 2 * R + 1];
+                    }
+                    float* o = H + (k & 1) * 32 * G::HP + hr * G::HP + g8;
+                    *(float4*)o = make_float4(h[0], h[1], h[2], h[3]);
+                    *(float4*)(o + 4) = make_float4(h[4], h[5], h[6], h[7]);
+                }
+                if (k > 0) {
+                    // the previous shift: (j - 1, sy), or the end of the previous row
+                    const int psx = j > 0 ? j - 1 - rho : rho;
+                    const int psy = j > 0 ? sy : sy - 1;
+                    vertical(k - 1, psx, psy, H + ((k - 1) & 1) * 32 * G::HP);
+                }
+                __syncthreads();
+                ++k;
+            }
+        }
+        vertical(W2 - 1, rho, rho, H + ((W2 - 1) & 1) * 32 * G::HP);
         __syncthreads();
-        if (sx == rho) { sx = -rho; ++sy; } else { ++sx; }
+    } else {
+        horizontal(-rho, -rho, H);
+        __syncthreads();
+        int sx = -rho, sy = -rho;
+        for (int k = 0; k < W2; ++k) {
+            if (k + 1 < W2) {
+                const int nx1 = (sx == rho) ? -rho : sx + 1;
+                const int ny1 = (sx == rho) ? sy + 1 : sy;
+                horizontal(nx1, ny1, H + ((k + 1) & 1) * 32 * G::HP);
+            }
+            vertical(k, sx, sy, H + (k & 1) * 32 * G::HP);
+            __syncthreads();
+            if (sx == rho) { sx = -rho; ++sy; } else { ++sx; }
+        }
     }
     // forward minima: owned by this thread
 #pragma unroll
@@ -245,18 +313,26 @@ __global__ void __launch_bounds__(256, 4) k_weights(WArgs a) {
 template <int R>
 static size_t weights_smem(int rho) { return sizeof(float) * WGeo<R>(rho).floats(); }
 
+// Shapes of the sliding-window pass 1: patch <= 7, window <= 15.
+constexpr int kSlideMaxR = 3;
+constexpr int kSlideMaxRho = 7;
+
 static cudaError_t prepare_gj_tma(int* slots);
 
 // Opt every weight-kernel variant into the largest dynamic shared memory any
 // window can need (called at geometry creation, outside any stream capture).
 cudaError_t prepare_weights(int* gj_slots) {
     cudaError_t e = cudaSuccess;
-#define TNLM_PREP_W(R)                                                                  \
+#define TNLM_PREP_W(R, SLIDE, RHO)                                                      \
     if (e == cudaSuccess)                                                               \
-        e = cudaFuncSetAttribute(k_weights<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                 (int)weights_smem<R>((kMaxWindow - 1) / 2));
-    TNLM_PREP_W(0) TNLM_PREP_W(1) TNLM_PREP_W(2) TNLM_PREP_W(3)
-    TNLM_PREP_W(4) TNLM_PREP_W(5) TNLM_PREP_W(6) TNLM_PREP_W(7)
+        e = cudaFuncSetAttribute(k_weights<R, SLIDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                 (int)weights_smem<R>(RHO));
+    TNLM_PREP_W(0, false, (kMaxWindow - 1) / 2) TNLM_PREP_W(1, false, (kMaxWindow - 1) / 2)
+    TNLM_PREP_W(2, false, (kMaxWindow - 1) / 2) TNLM_PREP_W(3, false, (kMaxWindow - 1) / 2)
+    TNLM_PREP_W(4, false, (kMaxWindow - 1) / 2) TNLM_PREP_W(5, false, (kMaxWindow - 1) / 2)
+    TNLM_PREP_W(6, false, (kMaxWindow - 1) / 2) TNLM_PREP_W(7, false, (kMaxWindow - 1) / 2)
+    TNLM_PREP_W(0, true, kSlideMaxRho) TNLM_PREP_W(1, true, kSlideMaxRho)
+    TNLM_PREP_W(2, true, kSlideMaxRho) TNLM_PREP_W(3, true, kSlideMaxRho)
 #undef TNLM_PREP_W
     return e == cudaSuccess ? prepare_gj_tma(gj_slots) : e;
 }
@@ -266,7 +342,13 @@ static cudaError_t launch_weights_r(const WArgs& a, cudaStream_t st) {
     using G = WGeo<R>;
     const size_t smem = weights_smem<R>(a.rho);
     dim3 grid((a.nx + G::TX - 1) / G::TX, (a.ny + G::TY - 1) / G::TY, a.N);
-    k_weights<R><<<grid, 256, smem, st>>>(a);
+    if constexpr (R <= kSlideMaxR) {
+        if (a.rho <= kSlideMaxRho) {
+            k_weights<R, true><<<grid, 256, smem, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
+    k_weights<R, false><<<grid, 256, smem, st>>>(a);
     return cudaGetLastError();
 }
 
