@@ -621,7 +621,15 @@ __global__ void __launch_bounds__(kGjvTx * kGjvTy) k_gj_vec(GjArgs a) {
 // are written per (tile, phase), so they do not depend on split or on the
 // tiles per CTA either.
 // ---------------------------------------------------------------------------
-constexpr int kTmaTW = 64, kTmaTH = 16;
+// Tile width 64 (64 x 16 tiles) or 128 (128 x 8, rows of 512 contiguous
+// bytes per box): measured at 512^2, W = 15, 0.554 against 0.549 ms per
+// sweep, 0.1016 against 0.1018 ms at 256^2 -- within noise, so the box
+// rows' DRAM locality is not what limits the sweep; 64 is kept.
+#ifndef TNLM_GJ_TW
+#define TNLM_GJ_TW 64
+#endif
+constexpr int kTmaTW = TNLM_GJ_TW, kTmaTH = 1024 / kTmaTW;   // 1024 pixels, 4 per consumer thread
+static_assert(kTmaTW == 64 || kTmaTW == 128, "sweep tile width");
 constexpr int kTmaBW = kTmaTW + 4;
 constexpr int kTmaConsumers = 256;
 constexpr int kTmaThreads = kTmaConsumers + 32;
@@ -768,7 +776,7 @@ __global__ void __launch_bounds__(kTmaThreads, 3) k_gj_tma(GjArgs a, const __gri
             s_uissued = nu;
         }
     } else {
-        const int tx = tid % 16, ty = tid / 16;
+        const int tx = tid % (kTmaTW / 4), ty = tid / (kTmaTW / 4);
         const size_t npx = (size_t)nx * ny;
         const float k2 = a.k2;
         bool bad = false, ok = true;
