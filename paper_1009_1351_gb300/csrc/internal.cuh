@@ -28,7 +28,10 @@ namespace tnlm {
 
 constexpr int kMaxPatch = 15;
 constexpr int kMaxWindow = 31;
-constexpr int kProjThreads = 256;     // rays per projector block
+#ifndef TNLM_PROJ_THREADS
+#define TNLM_PROJ_THREADS 128
+#endif
+constexpr int kProjThreads = TNLM_PROJ_THREADS;   // rays per projector block
 constexpr int kWTileX = 32, kWTileY = 16;  // weight kernel output tile
 constexpr int kGjTileX = 32, kGjTileY = 8; // Gauss-Jacobi tile
 

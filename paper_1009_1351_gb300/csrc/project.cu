@@ -139,10 +139,12 @@ cudaError_t launch_prep_dual_update(const tnlm_geometry* g, const float* s, floa
 // with kProjWarpsPerView warps of 32 adjacent bins.  Consecutive views of a
 // phase are a small rotation apart, so their rays march over nearly the same
 // pixels at the same time and the block's warps share the gathered lines in
-// L1.  Measured per launch (512^2, 888 bins; 1 / 2 / 4 / 8 views per block):
-// 360 views 0.880 / 0.794 / 0.751 / 0.744 ms, 90 views 0.305 / 0.285 / 0.281
-// / 0.289 ms; 4 is kept (8 leaves most warps of the last group idle when the
-// view count is not a multiple of 8).
+// L1.  Measured per launch (512^2, 888 bins), 256-thread blocks with 1 / 2
+// / 4 / 8 views: 360 views 0.880 / 0.794 / 0.751 / 0.744 ms, 90 views 0.305
+// / 0.285 / 0.281 / 0.289 ms (8 leaves most warps of the last group idle
+// when the view count is not a multiple of 8); with 4 views, 128 / 256 / 512
+// threads (one / two / four warps per view): 0.725 / 0.754 / 0.823 ms at
+// 360 views, 0.275 / 0.281 / 0.298 ms at 90.  Kept: 4 views, one warp each.
 #ifndef TNLM_PROJ_VPB
 #define TNLM_PROJ_VPB 4
 #endif
@@ -150,6 +152,7 @@ constexpr int kProjViews = TNLM_PROJ_VPB;
 static_assert(kProjViews == 1 || kProjViews == 2 || kProjViews == 4 || kProjViews == 8,
               "views per projector block");
 constexpr int kProjWarpsPerView = kProjThreads / 32 / kProjViews;
+static_assert(kProjWarpsPerView >= 1, "projector block smaller than its views");
 constexpr int kProjBinsPerBlock = 32 * kProjWarpsPerView;
 
 struct ProjArgs {
