@@ -314,7 +314,15 @@ cudaError_t launch_project(const tnlm_geometry* g, const float* R, const float* 
 // K2
 // ---------------------------------------------------------------------------
 constexpr int kBpT = 32;        // tile side
-constexpr int kBpWarps = 8;     // per block: kBpClassWarps per ray class
+// Warps per backprojector block, half per ray class.  Measured per launch
+// at 512^2 (360 / 90 views): 4 warps 1.313 / 0.362 ms, 8 warps 1.254 /
+// 0.338 ms, 12 warps 1.261 / 0.352 ms; 8 is kept.
+#ifndef TNLM_BP_WARPS
+#define TNLM_BP_WARPS 8
+#endif
+constexpr int kBpWarps = TNLM_BP_WARPS;     // per block: kBpClassWarps per ray class
+static_assert(kBpWarps % 2 == 0 && kBpWarps >= 2 && kBpWarps <= 16, "backprojector warps");
+constexpr int kBpMinBlocks = 40 / kBpWarps > 0 ? 40 / kBpWarps : 1;   // about 40 resident warps per SM
 constexpr int kBpClassWarps = kBpWarps / 2;
 constexpr int kBpMaxGroups = 4;  // view groups per tile (CTAs per tile)
 
@@ -358,7 +366,7 @@ __device__ __forceinline__ void deposit(float* acc, float kk, float am, float ik
 // DIRECT: the block sees all views of its tile and writes the image (and the
 // squared-norm partial); otherwise it writes its view group's partial image.
 template <bool DIRECT, bool PART>
-__global__ void __launch_bounds__(kBpWarps * 32, 5) k_backproject(BpArgs a) {
+__global__ void __launch_bounds__(kBpWarps * 32, kBpMinBlocks) k_backproject(BpArgs a) {
     extern __shared__ float sm[];
     float* acc = sm;                                    // [warp][32][32]
     float* tsum = acc + kBpWarps * kBpT * kBpT;         // [row][col + 1]
