@@ -165,7 +165,7 @@ def roofline_units(case, cls: str):
 def measured_traffic(cls: str, case_names):
     """Mean DRAM bytes per launch of a kernel class over the given cases, from
     the ncu captures listed in profiles/traffic.txt, or None when a case is
-    missing or the kernel's source file has changed since the capture."""
+    missing or a source file the capture depends on has changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
@@ -181,8 +181,15 @@ def measured_traffic(cls: str, case_names):
         r = rows.get((cls, c))
         if r is None:
             return None
-        src = os.path.join(ROOT, r[1])
-        if not os.path.exists(src) or hashlib.sha1(open(src, "rb").read()).hexdigest()[:12] != r[2]:
+        # the source column lists the files the counters depend on, joined
+        # by '+'; the hash is over their contents in that order
+        h = hashlib.sha1()
+        for part in r[1].split("+"):
+            src = os.path.join(ROOT, part)
+            if not os.path.exists(src):
+                return None
+            h.update(open(src, "rb").read())
+        if h.hexdigest()[:12] != r[2]:
             return None
         vals.append(r[0])
     return float(np.mean(vals))
