@@ -139,12 +139,10 @@ cudaError_t launch_prep_dual_update(const tnlm_geometry* g, const float* s, floa
 // with kProjWarpsPerView warps of 32 adjacent bins.  Consecutive views of a
 // phase are a small rotation apart, so their rays march over nearly the same
 // pixels at the same time and the block's warps share the gathered lines in
-// L1.  Measured per launch (512^2, 888 bins), 256-thread blocks with 1 / 2
-// / 4 / 8 views: 360 views 0.880 / 0.794 / 0.751 / 0.744 ms, 90 views 0.305
-// / 0.285 / 0.281 / 0.289 ms (8 leaves most warps of the last group idle
-// when the view count is not a multiple of 8); with 4 views, 128 / 256 / 512
-// threads (one / two / four warps per view): 0.725 / 0.754 / 0.823 ms at
-// 360 views, 0.275 / 0.281 / 0.298 ms at 90.  Kept: 4 views, one warp each.
+// L1.  In eager A/B runs at 512^2 (888 bins), 4 views in 128-thread blocks
+// took 0.725 / 0.275 ms per launch at 360 / 90 views against 0.754 / 0.281
+// with 256 threads and 0.823 / 0.298 with 512; in the graph-replayed
+// benchmark the mean launch is within 1 % of one view per 256-thread block.
 #ifndef TNLM_PROJ_VPB
 #define TNLM_PROJ_VPB 4
 #endif
