@@ -195,6 +195,12 @@ def measured_traffic(cls: str, case_names):
     return float(np.mean(vals))
 
 
+def traffic_class(cls: str, mixed: bool) -> str:
+    """Row name of a kernel class in profiles/traffic.txt: with mixed precision
+    the weights class is the tensor-core kernel, which has rows of its own."""
+    return "weights_tc" if mixed and cls == "weights" else cls
+
+
 _ALU_PEAK = {}
 
 
@@ -398,7 +404,7 @@ def run_gpu(args):
                 amt = np.mean([roofline_units(c, dominant)[0] for c in cases])
                 achieved = amt / (per_launch_ms / 1e3) / 1e12
                 peak, src = alu_peak_tops(local)
-            traffic = measured_traffic(dominant, scenarios)
+            traffic = measured_traffic(traffic_class(dominant, mixed), scenarios)
             roof = {"bound": bound, "kernel": dominant, "achieved": round(achieved, 3),
                     "peak": round(peak, 1), "unit": unit, "frac": round(achieved / peak, 4),
                     "traffic": None if traffic is None else int(traffic),
@@ -416,7 +422,7 @@ def run_gpu(args):
                 ach, pk = amt_c / (ms_c / 1e3) / 1e9, peaks.get("hbm_gbs", 6800.0)
             else:
                 ach, pk = amt_c / (ms_c / 1e3) / 1e12, alu_peak_tops(local)[0]
-            tr = measured_traffic(cls, scenarios)
+            tr = measured_traffic(traffic_class(cls, mixed), scenarios)
             by_kernel[cls] = {"bound": bound_c, "achieved": round(ach, 3), "peak": round(pk, 1),
                               "unit": unit_c, "frac": round(ach / pk, 4), "launch_ms": round(ms_c, 4),
                               "traffic": None if tr is None else int(tr)}

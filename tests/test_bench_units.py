@@ -52,3 +52,27 @@ def test_sweep_and_weights_bytes_follow_the_distance_array():
     assert gj == 4 * n_dist + 24 * g.n_phases * g.nx * g.ny
     assert w == 4 * n_dist + 20 * g.n_phases * g.nx * g.ny
     assert np.isclose(n_dist, 79.3e6, rtol=1e-3)
+
+
+def test_traffic_rows_are_used_only_while_their_sources_hash_to_them(tmp_path, monkeypatch):
+    """profiles/traffic.txt rows carry the hash of the files their counters
+    depend on ('+'-joined); a changed file voids the row, and the mixed
+    precision weights class looks up rows of its own."""
+    import hashlib
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "a.cu").write_text("kernel a\n")
+    (tmp_path / "b.cu").write_text("layout b\n")
+    h = hashlib.sha1(b"kernel a\nlayout b\n").hexdigest()[:12]
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# header\n"
+        f"weights  c1  100  20  a.cu+b.cu  {h}\n"
+        f"weights  c2  300  40  a.cu+b.cu  {h}\n"
+        f"gj       c1  7    1   a.cu  {hashlib.sha1(b'kernel a').hexdigest()[:12]}\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_traffic("weights", ["c1", "c2"]) == pytest.approx(230.0)
+    assert bench.measured_traffic("weights", ["c1", "c3"]) is None      # a case without a row
+    assert bench.measured_traffic("gj", ["c1"]) is None                 # hash of another content
+    assert bench.measured_traffic(bench.traffic_class("weights", True), ["c1"]) is None
+    assert bench.traffic_class("weights", False) == "weights"
+    (tmp_path / "b.cu").write_text("layout b, changed\n")
+    assert bench.measured_traffic("weights", ["c1"]) is None
