@@ -166,11 +166,13 @@ def normalised_from_gpu(D, norm, W, h):
 
 @pytest.mark.parametrize("shape,d,W", [((4, 21, 35), 3, 5), ((3, 40, 70), 5, 11),
                                        ((3, 37, 45), 7, 15), ((5, 17, 33), 1, 3),
-                                       ((3, 512, 512), 5, 11)])
+                                       ((3, 512, 512), 5, 11), ((3, 30, 41), 9, 5),
+                                       ((3, 29, 50), 3, 17)])
 def test_weights_match_oracle(tn, oracle_mod, shape, d, W):
-    """Small shapes split each tile's shifts over several CTAs (minima
-    combined by atomic min); 512 x 512 x 3 has enough tiles for one CTA per
-    tile and phase."""
+    """Ragged shapes (partial tiles, backward minima combined across tiles by
+    the integer atomic min) and 512 x 512 x 3; patch <= 7 with window <= 15
+    takes the sliding-window horizontal pass, the last two cases (patch 9,
+    window 17) the reloading one."""
     N, ny, nx = shape
     geom = synth.Geometry(nx=nx, ny=ny, pixel_mm=min(1.0, 128.0 / max(nx, ny)), n_phases=N, n_views=4,
                           n_bins=16, bin_mm=1.0, sid_mm=500.0, sdd_mm=800.0)
