@@ -82,3 +82,69 @@ def header_fields(cname):
 @pytest.mark.parametrize("cname", list(STRUCTS))
 def test_binding_has_every_header_field_in_order(cname):
     assert [f for f, _ in STRUCTS[cname]._fields_] == header_fields(cname)
+
+
+# ------------------------------------------------------------ prototypes
+_SCALARS = {"int": ctypes.c_int, "unsigned": ctypes.c_uint, "unsigned int": ctypes.c_uint,
+            "long": ctypes.c_long, "long long": ctypes.c_longlong, "double": ctypes.c_double,
+            "float": ctypes.c_float, "size_t": ctypes.c_size_t}
+
+
+def header_prototypes():
+    """{name: (return type, [parameter types])} of every tnlm_* function the
+    headers declare (comments removed, parameter names dropped)."""
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    out = {}
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(tnlm_[a-z_0-9]+)\s*\(([^;{}]*?)\)\s*;", src):
+        ret, name, args = " ".join(m.group(1).split()), m.group(2), " ".join(m.group(3).split())
+        params = [] if args in ("", "void") else [a.strip() for a in args.split(",")]
+        out[name] = (ret.replace("extern", "").strip(), params)
+    return out
+
+
+def c_param_kind(decl):
+    """'pointer', or the ctypes class of a scalar parameter declaration."""
+    if "*" in decl:
+        return "pointer"
+    words = decl.replace("const", " ").split()
+    base = " ".join(words[:-1])          # drop the parameter name
+    return _SCALARS.get(base, base)
+
+
+def ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(t, ctypes._Pointer):
+        return "pointer"
+    return t
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1009_1351_gb300 import build as tnbuild
+    tnbuild.build()
+    return tn.load_library()
+
+
+_RETURNS = {"tnlm_status": ctypes.c_int, "int": ctypes.c_int, "void": None,
+            "const char*": ctypes.c_char_p, "long long": ctypes.c_longlong}
+
+
+def test_argtypes_follow_the_prototypes(lib):
+    """Every function the binding gives argtypes takes as many arguments as
+    its prototype, pointers where the prototype has pointers and the same
+    scalar types elsewhere; functions without argtypes take no argument; and
+    every return type is the one ctypes reads."""
+    protos = header_prototypes()
+    assert set(protos) == set(tn.EXPORTED)
+    for name, (ret, params) in protos.items():
+        assert getattr(lib, name).restype is _RETURNS[" ".join(ret.replace("*", " * ").split())
+                                                      .replace(" *", "*")], name
+        at = getattr(lib, name).argtypes
+        if at is None:
+            assert params == [], name
+            continue
+        assert len(at) == len(params), name
+        for t, decl in zip(at, params):
+            assert ctypes_kind(t) == c_param_kind(decl), (name, decl)
