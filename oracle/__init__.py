@@ -25,29 +25,41 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "tnlm_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
+# A test that plants a mistake compiles a changed copy of tnlm_oracle.c and
+# points this variable at it (tests/test_oracle_mutations.py); the pins then
+# run against that copy.
+_LIB_OVERRIDE = os.environ.get("TNLM_ORACLE_LIB")
 _lib = None
+
+# the compiler flags of the oracle (FP64, no fast-math, no FMA contraction)
+CFLAGS = ["-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off", "-std=c11"]
 
 _dp = ctypes.POINTER(ctypes.c_double)
 _ip = ctypes.POINTER(ctypes.c_int)
 _lp = ctypes.POINTER(ctypes.c_long)
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile one oracle source file into a shared library at 'out'."""
+    subprocess.run(["gcc"] + CFLAGS + [src, "-o", out + ".tmp", "-lm"], check=True)
+    os.replace(out + ".tmp", out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle (gcc, FP64, no fast-math, no FMA contraction)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-std=c11", _SRC, "-o", _LIB + ".tmp", "-lm"]
-        subprocess.run(cmd, check=True)
-        os.replace(_LIB + ".tmp", _LIB)
+        compile_source(_SRC, _LIB)
     return _LIB
 
 
 def _load():
     global _lib
     if _lib is None:
-        build()
-        lib = ctypes.CDLL(_LIB)
+        lib = ctypes.CDLL(build())
         lib.orc_threads.restype = ctypes.c_int
         lib.orc_ray_entries.restype = ctypes.c_int
         lib.orc_objective_op.restype = ctypes.c_double
