@@ -6,8 +6,11 @@ changed copy with the oracle's own flags, and runs the oracle's pin tests
 (projector, weights, solvers, outer-loop step order) against it in a fresh
 pytest process (TNLM_ORACLE_LIB points the oracle package at the copy).
 At least one pin must fail for every case; the unchanged source, compiled
-the same way, must pass them all.  The mistakes are planted in the oracle,
-on the CPU; no GPU code is involved.
+the same way, must pass them all.  The network oracle (unet_oracle.py) is
+treated the same way: each changed copy is loaded as a module and its pins
+(correlation, identity, adjoint pairs, finite-difference gradients, BF16
+rounding) run against it.  The mistakes are planted in the oracle, on the
+CPU; no GPU code is involved.
 """
 import os
 import subprocess
@@ -91,3 +94,58 @@ def test_planted_mistake_fails_a_pin(tmp_path, source, name):
     assert text != source
     r = run_pins(tmp_path, text, name)
     assert r.returncode == 1, f"no pin caught '{name}':\n{r.stdout[-2000:]}"
+
+
+# ---------------------------------------------------------------- network oracle
+UNET_SRC = os.path.join(ROOT, "oracle", "unet_oracle.py")
+UNET_MUTATIONS = {
+    "convolution_instead_of_correlation": [
+        ('out += np.einsum("bchw,oc->bohw", xp[:, :, ky:ky + H, kx:kx + W], w[:, :, ky, kx])',
+         'out += np.einsum("bchw,oc->bohw", xp[:, :, ky:ky + H, kx:kx + W], w[:, :, 2 - ky, 2 - kx])', 0)],
+    "weight_gradient_taps_transposed": [("gw[:, :, ky, kx] = ", "gw[:, :, kx, ky] = ", 0)],
+    "relu_mask_dropped_in_the_decoder": [("g2 = g * (a2 > 0)", "g2 = g", 0)],
+    "upsampling_adjoint_averages": [("return g.reshape(B, C, H // 2, 2, W // 2, 2).sum(axis=(3, 5))",
+                                     "return g.reshape(B, C, H // 2, 2, W // 2, 2).mean(axis=(3, 5))", 0)],
+    "bf16_truncates": [("r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = (u >> 16) << 16", 0)],
+    "no_residual_input": [("out = xin + np.einsum(", "out = 0.0 * xin + np.einsum(", 0)],
+    "loss_gradient_halved": [("g_out = 2.0 * (out - target) / n", "g_out = (out - target) / n", 0)],
+}
+
+
+def load_module(text, name):
+    import types
+    mod = types.ModuleType(name)
+    exec(compile(text, name, "exec"), mod.__dict__)
+    return mod
+
+
+def unet_pins():
+    import test_oracle_unet as t
+    return [t.test_conv3_is_a_padded_correlation, t.test_zero_final_layer_gives_the_identity,
+            t.test_pool_and_upsample_adjoint_pairs, t.test_gradients_match_finite_differences,
+            t.test_bf16_rounding_is_nearest_even]
+
+
+def test_unchanged_network_oracle_passes_its_pins():
+    pytest.importorskip("scipy.signal")
+    mod = load_module(open(UNET_SRC).read(), "unet_unchanged")
+    for pin in unet_pins():
+        pin(mod)
+
+
+@pytest.mark.parametrize("name", list(UNET_MUTATIONS))
+def test_planted_network_mistake_fails_a_pin(name):
+    pytest.importorskip("scipy.signal")
+    source = open(UNET_SRC).read()
+    text = source
+    for old, new, n in UNET_MUTATIONS[name]:
+        text = replace_nth(text, old, new, n)
+    assert text != source
+    mod = load_module(text, "unet_" + name)
+    failed = []
+    for pin in unet_pins():
+        try:
+            pin(mod)
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"no pin caught '{name}'"
