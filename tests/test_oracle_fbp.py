@@ -11,10 +11,12 @@ import pytest
 from paper_1009_1351_gb300 import synth
 
 
-def disc_case(L, V, B, fov=64.0, cx=5.0, cy=-3.0, R=18.0, mu=0.02, N=3):
+def disc_case(L, V, B, fov=64.0, cx=5.0, cy=-3.0, R=18.0, mu=0.02, N=3, sid=500.0, sdd=750.0,
+              bin_mm=None):
     pix = fov / L
     g = synth.Geometry(nx=L, ny=L, pixel_mm=pix, n_phases=N, n_views=V, n_bins=B,
-                       bin_mm=fov * 1.2 / B * 1.5, sid_mm=500.0, sdd_mm=750.0)
+                       bin_mm=fov * 1.2 / B * 1.5 if bin_mm is None else bin_mm,
+                       sid_mm=sid, sdd_mm=sdd)
     src, d = synth.ray_endpoints(g)
     p = np.abs((src[..., 0] - cx) * d[..., 1] - (src[..., 1] - cy) * d[..., 0])
     y = 2.0 * mu * np.sqrt(np.maximum(R * R - p * p, 0.0))
@@ -24,8 +26,8 @@ def disc_case(L, V, B, fov=64.0, cx=5.0, cy=-3.0, R=18.0, mu=0.02, N=3):
     return g, y, r, mu, R
 
 
-def disc_errors(oracle_mod, L, V, B):
-    g, y, r, mu, R = disc_case(L, V, B)
+def disc_errors(oracle_mod, L, V, B, **geo):
+    g, y, r, mu, R = disc_case(L, V, B, **geo)
     f = oracle_mod.fbp(oracle_mod.Geom(g), y)
     inner = f[0][r < R - 4 * g.pixel_mm]
     outer = f[0][(r > R + 4 * g.pixel_mm) & (r < 28.0)]
@@ -37,6 +39,16 @@ def test_fbp_recovers_a_uniform_disc(oracle_mod):
     assert bias < 0.01
     assert out < 0.02
     assert noise < 0.02
+
+
+def test_fbp_recovers_a_uniform_disc_in_a_wide_fan(oracle_mod):
+    """Source 80 mm from the isocentre of a 64 mm field: fan angles up to
+    34 degrees, where the equiangular algorithm's cos(gamma) pre-weighting
+    matters (without it the interior spread is ~1 %, with it ~0.03 %)."""
+    bias, out, noise, f = disc_errors(oracle_mod, 64, 180, 160, sid=80.0, sdd=130.0, bin_mm=1.25)
+    assert bias < 1e-3
+    assert out < 0.02
+    assert noise < 2e-3
 
 
 def test_fbp_gives_every_phase_the_same_image(oracle_mod):

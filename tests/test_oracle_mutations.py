@@ -3,7 +3,8 @@
 Each case below changes tnlm_oracle.c in one plausible way -- a sign, an
 index, a dropped factor or term, a misread step order -- compiles the
 changed copy with the oracle's own flags, and runs the oracle's pin tests
-(projector, weights, solvers, outer-loop step order) against it in a fresh
+(projector, weights, solvers, outer-loop step order, Eq. 1's terms, FBP)
+against it in a fresh
 pytest process (TNLM_ORACLE_LIB points the oracle package at the copy).
 At least one pin must fail for every case; the unchanged source, compiled
 the same way, must pass them all.  The network oracle (unet_oracle.py) is
@@ -22,7 +23,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(ROOT, "oracle", "tnlm_oracle.c")
 PINS = [os.path.join(HERE, f) for f in ("test_oracle_projector.py", "test_oracle_weights.py",
-                                        "test_oracle_solvers.py", "test_oracle_outer_loop.py")]
+                                        "test_oracle_solvers.py", "test_oracle_outer_loop.py",
+                                        "test_oracle_objective.py", "test_oracle_fbp.py")]
 
 # name -> list of (text, replacement, which occurrence)
 MUTATIONS = {
@@ -51,6 +53,15 @@ MUTATIONS = {
     "jacobi_from_the_previous_iterate": [("orc_gj(NPH, NX, NY, W, g, use_n, use_p, mu_hat, m2, fn);",
                                           "orc_gj(NPH, NX, NY, W, f, use_n, use_p, mu_hat, m2, fn);", 0)],
     "no_positivity_step": [("if (fn[q] < 0.0) fn[q] = 0.0;", "if (fn[q] < -1e300) fn[q] = 0.0;", 0)],
+    "tnlm_term_neighbours_swapped": [("const int j = dir == 0 ? (i + N - 1) % N : (i + 1) % N;",
+                                      "const int j = dir == 0 ? (i + 1) % N : (i + N - 1) % N;", 0)],
+    "tnlm_term_unsquared": [("J += dv * dv * w[", "J += fabs(dv) * w[", 0)],
+    "data_term_sqrt_w": [("data += w[k] * (t[k] - y[k]) * (t[k] - y[k]);",
+                          "data += sqrt(w[k]) * (t[k] - y[k]) * (t[k] - y[k]);", 1)],
+    "fbp_angular_step_halved": [("const double dbeta = 2.0 * ORC_PI / (double)M;",
+                                 "const double dbeta = ORC_PI / (double)M;", 0)],
+    "fbp_no_cosine_weight": [("acc += y[v * B + k] * SID * cos(gk) * c[n - k + B - 1];",
+                              "acc += y[v * B + k] * SID * c[n - k + B - 1];", 0)],
 }
 
 
