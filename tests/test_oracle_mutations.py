@@ -53,6 +53,10 @@ MUTATIONS = {
     "jacobi_from_the_previous_iterate": [("orc_gj(NPH, NX, NY, W, g, use_n, use_p, mu_hat, m2, fn);",
                                           "orc_gj(NPH, NX, NY, W, f, use_n, use_p, mu_hat, m2, fn);", 0)],
     "no_positivity_step": [("if (fn[q] < 0.0) fn[q] = 0.0;", "if (fn[q] < -1e300) fn[q] = 0.0;", 0)],
+    "gradient_step_sign": [("g[k] = f[k] - g[k] / beta;", "g[k] = f[k] + g[k] / beta;", 0)],
+    "cgls_a_inverted": [("else a[i] = gam[i] / den;", "else a[i] = den / gam[i];", 0)],
+    "cgls_residual_not_updated": [("r[i * nsg + k] -= a[i] * t[i * nsg + k];",
+                                   "r[i * nsg + k] -= 0.0 * t[i * nsg + k];", 0)],
     "tnlm_term_neighbours_swapped": [("const int j = dir == 0 ? (i + N - 1) % N : (i + 1) % N;",
                                       "const int j = dir == 0 ? (i + 1) % N : (i + N - 1) % N;", 0)],
     "tnlm_term_unsquared": [("J += dv * dv * w[", "J += fabs(dv) * w[", 0)],
