@@ -131,14 +131,17 @@ typedef struct {
     double* objective_hist;  /* Eq. 1 after every iteration */
 } tnlm_report;
 
-/* Create a geometry handle on desc->device.  The library copies the view
- * angles and builds its per-view / per-bin / per-ray tables on the device.
+/* Create a geometry handle on desc->device: the fan-beam scan of Sec. 3
+ * (a source on a circle, an equiangular arc detector, N phases of V views)
+ * that P_i of Eq. 1 projects along.  The library copies the view angles and
+ * builds its per-view / per-bin / per-ray tables on the device.
  * Errors: TNLM_ERR_INVALID_ARG (see the field comments above), TNLM_ERR_OOM,
  * TNLM_ERR_CUDA.  *out is NULL on failure. */
 tnlm_status tnlm_create_geometry(const tnlm_geometry_desc* desc, tnlm_geometry** out);
 
-/* Free the handle, its tables and its cached workspace.  NULL is a no-op.
- * Synchronises the handle's device. */
+/* Free the handle, its tables and its cached workspace (no counterpart in
+ * the paper: resource management).  NULL is a no-op.  Synchronises the
+ * handle's device. */
 void tnlm_destroy_geometry(tnlm_geometry* geom);
 
 /* d_sino[i] = P_i d_img[i] for every phase (Eq. 1).  In: image [N][ny][nx];
@@ -192,7 +195,8 @@ tnlm_status tnlm_fbp(const tnlm_geometry* geom, const float* d_y, float* d_img, 
  * Layout, ownership and errors as tnlm_fbp. */
 tnlm_status tnlm_fbp_phases(const tnlm_geometry* geom, const float* d_y, float* d_img, void* stream);
 
-/* Byte sizes of the two output buffers of tnlm_weights. */
+/* Byte sizes of the two output buffers of tnlm_weights (Eq. 8 distances
+ * for the W x W window of Sec. 2.3, and the per-direction normalisers). */
 tnlm_status tnlm_weights_size(const tnlm_geometry* geom, const tnlm_params* params,
                               size_t* dist_bytes, size_t* norm_bytes);
 
@@ -214,7 +218,8 @@ tnlm_status tnlm_weights(const tnlm_geometry* geom, const tnlm_params* params, c
                          float* d_dist, float* d_norm, void* stream);
 
 /* Workspace the handle allocates for tnlm_reconstruct / tnlm_weights with
- * these parameters (it is cached and reused between calls). */
+ * these parameters (it is cached and reused between calls; no counterpart
+ * in the paper: the storage of the TNLM box's intermediate arrays). */
 tnlm_status tnlm_workspace_bytes(const tnlm_geometry* geom, const tnlm_params* params,
                                  size_t* bytes);
 
@@ -279,7 +284,8 @@ tnlm_status tnlm_reconstruct_batch(tnlm_geometry* const* geoms, const tnlm_param
                                    void* stream);
 
 /* 1 if the last tnlm_reconstruct_batch call on this host thread ran as a
- * single loop-graph launch, else 0. */
+ * single loop-graph launch, else 0 (no counterpart in the paper: how the
+ * batched TNLM boxes were launched). */
 int tnlm_batch_last_was_loop(void);
 
 /* Kernel classes, for launch counting and optional device timing. */
@@ -293,14 +299,16 @@ enum {
     TNLM_KCLASS_COUNT = 6
 };
 
-/* Profiling (tracing) of the handle's kernels.  Launches of every class are
+/* Profiling (tracing) of the handle's kernels (no counterpart in the
+ * paper; the classes are the steps of the TNLM box).  Launches of every class are
  * always counted on the host.  Classes in class_mask (bit c = class c) are
  * additionally bracketed by CUDA events recorded on the launch stream, so
  * their device time can be read back; 0 turns the timing off.  Timing adds
  * two event records per timed launch. */
 tnlm_status tnlm_profile_enable(tnlm_geometry* geom, unsigned int class_mask);
 
-/* ms[TNLM_KCLASS_COUNT]: summed device time (ms) of the timed launches per
+/* Read the profile (no counterpart in the paper).
+ * ms[TNLM_KCLASS_COUNT]: summed device time (ms) of the timed launches per
  * class; launches[TNLM_KCLASS_COUNT]: launches per class; either may be NULL.
  * Synchronises the handle's device.  reset != 0 clears both afterwards. */
 tnlm_status tnlm_profile_read(tnlm_geometry* geom, double* ms, long long* launches, int reset);
@@ -317,15 +325,17 @@ tnlm_status tnlm_profile_read(tnlm_geometry* geom, double* ms, long long* launch
  * buffer.  Errors: TNLM_ERR_OOM, TNLM_ERR_CUDA. */
 tnlm_status tnlm_measure_peaks(int device, double* fp32_ops, double* ex2_ops);
 
-/* Message of the last failing call on this host thread ("" if none). */
+/* Message of the last failing call on this host thread ("" if none; no
+ * counterpart in the paper: error reporting). */
 const char* tnlm_last_error(void);
 
-/* Test hook for failure handling: the n-th device allocation from now on
- * (n >= 1) fails as if the device were out of memory; n = 0 disables. */
+/* Test hook for failure handling (no counterpart in the paper): the n-th
+ * device allocation from now on (n >= 1) fails as if the device were out of
+ * memory; n = 0 disables. */
 void tnlm_debug_fail_alloc_after(int n);
 
-/* Test hook for the timeout path: the pipeline waits of the TMA
- * Gauss-Jacobi sweep give up after 'polls' polls of their mbarrier (< 0:
+/* Test hook for the timeout path (no counterpart in the paper): the
+ * pipeline waits of the TMA Gauss-Jacobi sweep (Eq. 7) give up after 'polls' polls of their mbarrier (< 0:
  * the built-in limit, 2^24).  A sweep whose wait gives up stops issuing
  * copies, waits (with the built-in limit) for the copies it has in flight,
  * leaves its outputs unwritten and sets the device flag that the next
